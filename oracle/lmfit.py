@@ -1,0 +1,232 @@
+"""Least-misfit gridding function C(u') and gridding correction h(x), FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+What the paper fixes (Section 3.3):
+
+* Eq. csum2 -- the misfit of one visibility whose grid offset is nu:
+  ``L(x, nu) = 1 - h(x) * sum_s C(s - nu) exp(2 pi i (s - nu) x)`` with
+  ``s = -(W-1)/2 .. (W-1)/2`` and ``-1/2 <= nu < 1/2`` (the paper prints the
+  upper limit as ``< -1/2``; it is read as ``< 1/2``).
+* Eq. norm_bound -- the error bound
+  ``E^2 = 1/(2 x0) * int_{-x0}^{x0} int_{-1/2}^{1/2} |L(x, nu)|^2 dnu dx`` and
+  the map error ``l(x) = int |L(x, nu)|^2 dnu``.
+* The least-misfit pair (C, h) is, for given W and x0, the even C supported on
+  ``[-W/2, W/2]`` and the real h that minimise E (the "Making a map" box of
+  Section 3.3; the construction itself is only cited there).
+
+How this module computes the minimiser (the paper gives no algorithm):
+
+* Write ``c_s(nu) = C(s - nu)`` for ``nu`` in ``[-1/2, 1/2]``.  For a fixed h,
+  the best ``c(nu)`` solves a linear least-squares problem whose matrix does
+  not depend on nu, so ``c_s(nu)`` is an entire function of nu; it is
+  represented exactly enough by a Legendre series in ``2 nu`` of degree D.
+  Evenness of C, ``C(u) = C(-u)``, is ``c_{-s}(nu) = c_s(-nu)`` and is built
+  into the parameterisation.
+* For fixed C the best h is pointwise in x:
+  ``h(x) = int Re a(x,nu) dnu / int |a(x,nu)|^2 dnu`` with
+  ``a(x, nu) = sum_s c_s(nu) exp(2 pi i (s - nu) x)``.  This defines h at any
+  argument, which is how ``h_z(z(x, y))`` is evaluated off any grid (the paper
+  interpolates a table instead, Section 5.3).
+* With h eliminated this way, the misfit is a function of the Legendre
+  coefficients alone, and its small residual makes Gauss-Newton converge in a
+  handful of iterations.  (Plain alternation between the two partial
+  minimisations converges to the same point but needs thousands of sweeps.)
+
+Pins (tests/test_oracle_lmfit.py): E(W=7, x0=0.25) against the quoted
+1.3e-7 (Section 6); the layer multipliers 6, 27, 500 quoted for Figure 3; the
+top-hat closed form of Section 6; evenness; W=1 against the top hat.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from functools import lru_cache
+
+import numpy as np
+from numpy.polynomial import legendre as _leg
+
+
+def gauss_legendre(n: int, a: float, b: float):
+    """n-point Gauss-Legendre nodes and weights on [a, b]."""
+    t, w = _leg.leggauss(n)
+    return 0.5 * (b - a) * t + 0.5 * (b + a), 0.5 * (b - a) * w
+
+
+def tap_offsets(W: int) -> np.ndarray:
+    """The W values s = -(W-1)/2 .. (W-1)/2 of Eq. csum2 (half-integers for even W)."""
+    return np.arange(W, dtype=np.float64) - 0.5 * (W - 1)
+
+
+@dataclass(frozen=True)
+class LeastMisfit:
+    """A least-misfit pair for width ``W`` and cropping parameter ``x0``.
+
+    ``beta[i, k]`` is the coefficient of the Legendre polynomial ``P_k(2 nu)``
+    in ``c_i(nu) = C(s_i - nu)``, ``s_i = i - (W-1)/2``.
+    """
+
+    W: int
+    x0: float
+    beta: np.ndarray          # (W, D+1)
+    E: float                  # error bound of Eq. norm_bound, fine quadrature
+    n_nu: int = 96            # nu-quadrature used to define h off-grid
+
+    @property
+    def degree(self) -> int:
+        return self.beta.shape[1] - 1
+
+    def weights(self, nu) -> np.ndarray:
+        """``c_i(nu)`` for every tap i: array of shape ``nu.shape + (W,)``."""
+        nu = np.asarray(nu, dtype=np.float64)
+        P = _leg.legvander(2.0 * nu, self.degree)          # (..., D+1)
+        return P @ self.beta.T
+
+    def h(self, x) -> np.ndarray:
+        """Gridding correction at arbitrary x (the h-step formula above)."""
+        x = np.asarray(x, dtype=np.float64)
+        flat = x.reshape(-1)
+        nq, wn = gauss_legendre(self.n_nu, -0.5, 0.5)
+        c = self.weights(nq)                               # (nn, W)
+        s = tap_offsets(self.W)
+        out = np.empty_like(flat)
+        step = 4096
+        for a0 in range(0, flat.size, step):
+            xs = flat[a0:a0 + step]
+            ph = 2.0 * np.pi * (s[None, None, :] - nq[None, :, None]) * xs[:, None, None]
+            a = (c[None, :, :] * np.exp(1j * ph)).sum(-1)    # (nx, nn)
+            R = (wn[None, :] * a.real).sum(1)
+            Q = (wn[None, :] * (a.real ** 2 + a.imag ** 2)).sum(1)
+            out[a0:a0 + step] = R / Q
+        return out.reshape(x.shape)
+
+
+def misfit_L(weights_fn, h_fn, W, x, nu):
+    """L(x, nu) of Eq. csum2 on the outer grid x (nx,) by nu (nn,)."""
+    s = tap_offsets(W)
+    c = weights_fn(nu)                                      # (nn, W)
+    ph = 2.0 * np.pi * (s[None, None, :] - nu[None, :, None]) * x[:, None, None]
+    a = (c[None, :, :] * np.exp(1j * ph)).sum(-1)
+    return 1.0 - h_fn(x)[:, None] * a
+
+
+def map_error(weights_fn, h_fn, W, x, n_nu=200):
+    """l(x) = int_{-1/2}^{1/2} |L(x, nu)|^2 dnu (Section 3.3)."""
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    nq, wn = gauss_legendre(n_nu, -0.5, 0.5)
+    L = misfit_L(weights_fn, h_fn, W, x, nq)
+    return (wn[None, :] * np.abs(L) ** 2).sum(1)
+
+
+def error_bound(weights_fn, h_fn, W, x0, nx=200, n_nu=200):
+    """E of Eq. norm_bound by tensor Gauss-Legendre quadrature."""
+    xq, wx = gauss_legendre(nx, -x0, x0)
+    ell = map_error(weights_fn, h_fn, W, xq, n_nu)
+    return float(np.sqrt((wx * ell).sum() / (2.0 * x0)))
+
+
+# -- top hat (Section 6: the original W-stacking seen as W_z = 1) -----------
+
+def tophat_weights(nu):
+    """C_z = 1 on |w'| < 1/2, so the single tap weight is 1 for every nu."""
+    nu = np.asarray(nu, dtype=np.float64)
+    return np.ones(nu.shape + (1,))
+
+
+def tophat_h(z):
+    """h(z) = 1 / sinc z with sinc z = sin(pi z)/(pi z)."""
+    return 1.0 / np.sinc(np.asarray(z, dtype=np.float64))
+
+
+# -- the fit ------------------------------------------------------------------
+
+def _parameter_map(W: int, D: int, nu: np.ndarray):
+    """Basis of the even parameterisation: B[p] is (nn, W), c = sum_p beta_p B[p]."""
+    s = tap_offsets(W)
+    P = _leg.legvander(2.0 * nu, D)                         # (nn, D+1)
+    cols = []
+    for i, si in enumerate(s):
+        if si < 0:
+            continue
+        for k in range(D + 1):
+            if si == 0 and k % 2:
+                continue                                    # c_0(nu) is even in nu
+            cols.append((i, k))
+    B = np.zeros((len(cols), nu.size, W))
+    for p, (i, k) in enumerate(cols):
+        B[p, :, i] += P[:, k]
+        j = W - 1 - i
+        if j != i:
+            # c_{-s}(nu) = c_s(-nu) and P_k(-2nu) = (-1)^k P_k(2nu)
+            B[p, :, j] += (-1.0) ** k * P[:, k]
+    return cols, B
+
+
+def _expand(cols, vec, W, D):
+    beta = np.zeros((W, D + 1))
+    for (i, k), b in zip(cols, vec):
+        beta[i, k] += b
+        j = W - 1 - i
+        if j != i:
+            beta[j, k] += (-1.0) ** k * b
+    return beta
+
+
+@lru_cache(maxsize=64)
+def least_misfit(W: int, x0: float, degree: int = 20, nx: int = 64,
+                 n_nu: int = 64, max_iter: int = 60) -> LeastMisfit:
+    """Minimise E over even C (support W) and real h for cropping parameter x0."""
+    if not (1 <= W <= 16) or not (0.0 < x0 <= 0.5):
+        raise ValueError("need 1 <= W <= 16 and 0 < x0 <= 0.5")
+    xq, wx = gauss_legendre(nx, -x0, x0)
+    nq, wn = gauss_legendre(n_nu, -0.5, 0.5)
+    s = tap_offsets(W)
+    cols, B = _parameter_map(W, degree, nq)
+    npar = len(cols)
+    E = np.exp(2j * np.pi * (s[None, None, :] - nq[None, :, None]) * xq[:, None, None])
+    A = np.einsum("pnw,xnw->pxn", B, E)                     # d a(x,nu) / d beta_p
+    sq = np.sqrt(wx[:, None] * wn[None, :])
+
+    def realify(Z):                                         # complex (p, x, n) -> real rows
+        Zw = sq[None] * Z
+        return np.concatenate([Zw.real.reshape(Z.shape[0], -1),
+                               Zw.imag.reshape(Z.shape[0], -1)], 1).T
+
+    def state(vec):
+        a = np.einsum("p,pxn->xn", vec, A)
+        R = (wn[None, :] * a.real).sum(1)
+        Q = (wn[None, :] * (a.real ** 2 + a.imag ** 2)).sum(1)
+        h = R / Q
+        rho = 1.0 - h[:, None] * a
+        obj = float((wx[:, None] * wn[None, :] * np.abs(rho) ** 2).sum() / (2.0 * x0))
+        return a, R, Q, h, rho, obj
+
+    # start: the best C for h = 1 (one exact partial minimisation)
+    y = np.concatenate([sq.ravel(), np.zeros(sq.size)])
+    vec = np.linalg.lstsq(realify(A), y, rcond=None)[0]
+    a, R, Q, h, rho, obj = state(vec)
+    for _ in range(max_iter):
+        dR = (wn[None, None, :] * A.real).sum(2)                                  # (p, x)
+        dQ = 2.0 * (wn[None, None, :] * (np.conj(a)[None] * A).real).sum(2)
+        dh = dR / Q[None] - (R / Q ** 2)[None] * dQ
+        J = -(dh[:, :, None] * a[None] + h[None, :, None] * A)
+        rr = np.concatenate([(sq * rho).real.ravel(), (sq * rho).imag.ravel()])
+        step = np.linalg.lstsq(realify(J), -rr, rcond=1e-14)[0]
+        lam, improved = 1.0, False
+        while lam > 1e-8:
+            cand = state(vec + lam * step)
+            if cand[-1] < obj:
+                improved = True
+                break
+            lam *= 0.5
+        if not improved:
+            break
+        rel = (obj - cand[-1]) / obj
+        vec = vec + lam * step
+        a, R, Q, h, rho, obj = cand
+        if rel < 1e-9:
+            break
+    beta = _expand(cols, vec, W, degree)
+    beta = beta * h[np.argmin(np.abs(xq))]                  # gauge: h(0) ~ 1 (h scales as 1/beta)
+    lm = LeastMisfit(W=W, x0=float(x0), beta=beta, E=float("nan"))
+    Efine = error_bound(lm.weights, lm.h, W, x0)
+    return LeastMisfit(W=W, x0=float(x0), beta=beta, E=Efine)

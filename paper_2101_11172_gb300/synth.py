@@ -1,0 +1,152 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds input generation only -- no gridding, transform or
+correction arithmetic -- so both the CUDA path and the FP64 oracle can be fed
+from it.  The paper's own data (VLA B-array at 74 MHz with a 34-source sky,
+Section 6.3; G55.7+3.4 and GMRT AMI001, Section 7) are not available, so these
+stand-ins reproduce their shape: earth-rotation uvw tracks of a non-coplanar
+array with a significant w range, and point-source skies.
+
+Every generator takes a seed and uses numpy's PCG64; a workload is seeded
+with ``SEED_BASE + index`` (index 0 = tiny, 1 = survey, 2 = reduced cost,
+3 = differentiable, 4 = batched).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 2101111720
+
+
+def rng_for(index: int, stream: int = 0) -> np.random.Generator:
+    """Independent sub-stream ``stream`` of workload ``index``."""
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE + index, stream])))
+
+
+def complex_normal(n: int, rng: np.random.Generator, sigma: float = 1.0) -> np.ndarray:
+    """CN(0, sigma^2): real and imaginary parts N(0, sigma^2/2)."""
+    s = sigma / math.sqrt(2.0)
+    return (rng.normal(0.0, s, n) + 1j * rng.normal(0.0, s, n)).astype(np.complex128)
+
+
+def point_sky(N: int, n_src: int, rng: np.random.Generator, lo=0.1, hi=1.0) -> np.ndarray:
+    """N x N image (rows = m, columns = l) with n_src unit-pixel sources at distinct pixels."""
+    img = np.zeros((N, N), dtype=np.complex128)
+    pos = rng.choice(N * N, size=n_src, replace=False)
+    img.ravel()[pos] = rng.uniform(lo, hi, n_src)
+    return img
+
+
+def blob_sky(N: int, n_points: int, n_blobs: int, rng: np.random.Generator) -> np.ndarray:
+    """Point sources plus circular Gaussian blobs (sigma 2-8 pixels)."""
+    img = point_sky(N, n_points, rng)
+    yy = np.arange(N)
+    for _ in range(n_blobs):
+        cy, cx = rng.uniform(0, N, 2)
+        sig = rng.uniform(2.0, 8.0)
+        amp = rng.uniform(0.1, 1.0)
+        r = int(math.ceil(5 * sig))
+        ys = yy[max(0, int(cy) - r): min(N, int(cy) + r + 1)]
+        xs = yy[max(0, int(cx) - r): min(N, int(cx) + r + 1)]
+        g = np.exp(-0.5 * (((ys[:, None] - cy) ** 2 + (xs[None, :] - cx) ** 2) / sig ** 2))
+        img[ys[0]:ys[-1] + 1, xs[0]:xs[-1] + 1] += amp * g
+    return img
+
+
+def disc_uvw(M: int, radius: float, w_half: float, rng: np.random.Generator) -> np.ndarray:
+    """(u, v) uniform in a disc of the given radius, w uniform in [-w_half, w_half]."""
+    r = radius * np.sqrt(rng.uniform(0.0, 1.0, M))
+    th = rng.uniform(0.0, 2 * math.pi, M)
+    w = rng.uniform(-w_half, w_half, M)
+    return np.stack([r * np.cos(th), r * np.sin(th), w], 1)
+
+
+def array_uvw(n_ant: int, diameter_m: float, lat_deg: float, dec_deg: float,
+              ha_hours: tuple, n_times: int, uv_max: float,
+              rng: np.random.Generator) -> np.ndarray:
+    """Earth-rotation tracks of a flat random array, scaled to max |(u,v)| = uv_max.
+
+    Antennas are uniform in a disc of the given diameter on the local
+    horizontal plane; baselines go local (east, north, up) -> equatorial
+    (X, Y, Z) -> (u, v, w) at each hour angle, the textbook interferometer
+    geometry.  The wavelength is chosen afterwards so that the longest
+    projected (u, v) equals ``uv_max`` wavelengths.  Rows are time-major.
+    """
+    rad = 0.5 * diameter_m * np.sqrt(rng.uniform(0.0, 1.0, n_ant))
+    th = rng.uniform(0.0, 2 * math.pi, n_ant)
+    east, north = rad * np.cos(th), rad * np.sin(th)
+    up = np.zeros(n_ant)
+    lat = math.radians(lat_deg)
+    X = -north * math.sin(lat) + up * math.cos(lat)
+    Y = east
+    Z = north * math.cos(lat) + up * math.sin(lat)
+    ia, ib = np.triu_indices(n_ant, k=1)
+    B = np.stack([X[ib] - X[ia], Y[ib] - Y[ia], Z[ib] - Z[ia]], 1)       # (nbl, 3) metres
+    H = np.radians(15.0 * np.linspace(ha_hours[0], ha_hours[1], n_times))
+    d = math.radians(dec_deg)
+    sH, cH = np.sin(H)[:, None], np.cos(H)[:, None]
+    Bx, By, Bz = B[None, :, 0], B[None, :, 1], B[None, :, 2]
+    u = sH * Bx + cH * By
+    v = -math.sin(d) * cH * Bx + math.sin(d) * sH * By + math.cos(d) * Bz
+    w = math.cos(d) * cH * Bx - math.cos(d) * sH * By + math.sin(d) * Bz
+    uvw = np.stack([u.ravel(), v.ravel(), w.ravel()], 1)
+    scale = uv_max / np.sqrt(uvw[:, 0] ** 2 + uvw[:, 1] ** 2).max()
+    return uvw * scale
+
+
+@dataclass
+class Workload:
+    name: str
+    N: int
+    x0: float
+    W: int
+    fov: float
+    uvw: np.ndarray
+    image: np.ndarray = field(repr=False)
+    vis: np.ndarray = field(repr=False)
+
+    @property
+    def M(self) -> int:
+        return self.uvw.shape[0]
+
+    @property
+    def w_range(self):
+        return float(self.uvw[:, 2].min()), float(self.uvw[:, 2].max())
+
+
+def tiny(variant: str = "A", N: int = 256, M: int = 10_000, fov: float = 0.2,
+         n_src: int = 50, W: int = 7, x0: float = 0.25) -> Workload:
+    """Plain method, tiny: N = 256 from a 512 grid, l, m in +-0.1 rad, 10^4 visibilities.
+
+    (u, v) uniform in a disc of radius R = 0.45 N / fov wavelengths; w uniform
+    in +-0.05 R N (variant "A", several hundred w-planes) or +-0.05 R
+    (variant "B", about ten planes); 50 point sources with amplitudes
+    U(0.1, 1) for degridding; CN(0, 1) visibilities for gridding.
+    """
+    R = 0.45 * N / fov
+    w_half = 0.05 * R * (N if variant == "A" else 1.0)
+    uvw = disc_uvw(M, R, w_half, rng_for(0, 1 if variant == "A" else 11))
+    image = point_sky(N, n_src, rng_for(0, 2))
+    vis = complex_normal(M, rng_for(0, 3))
+    return Workload(f"tiny-{variant}", N, x0, W, fov, uvw, image, vis)
+
+
+def survey(N: int = 2048, n_ant: int = 256, n_times: int = 306, fov: float = 0.5,
+           W: int = 7, x0: float = 0.25, sigma: float = 0.01, index: int = 1,
+           ha_hours=(-4.0, 4.0)) -> Workload:
+    """Survey-scale plain method: 256 antennas in a 10 km disc, 8 h tracks at dec -30.
+
+    32,640 baselines x 306 times = 9,987,840 visibilities; latitude -30 deg
+    (unstated in the workload, a reading); max |(u,v)| = 0.45 N / fov; sky of
+    500 points plus 20 Gaussian blobs; visibilities to grid are CN(0, 1) plus
+    CN(0, sigma^2) noise, stored as complex64.
+    """
+    uvw = array_uvw(n_ant, 10_000.0, -30.0, -30.0, ha_hours, n_times,
+                    0.45 * N / fov, rng_for(index, 1))
+    image = blob_sky(N, 500, 20, rng_for(index, 2))
+    M = uvw.shape[0]
+    vis = complex_normal(M, rng_for(index, 3)) + complex_normal(M, rng_for(index, 4), sigma)
+    return Workload(f"survey-N{N}-M{M}", N, x0, W, fov, uvw, image, vis)

@@ -1,0 +1,87 @@
+"""Pins of the FP64 least-misfit fit against what the paper and mathematics fix."""
+import math
+
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from oracle.lmfit import (error_bound, least_misfit, map_error, tophat_h, tophat_weights)
+
+
+def test_error_bound_W7_x0_quarter(golden):
+    # Section 6.1: E = 1.3e-7 for W = 7, x0 = 0.25.  The exact minimiser of
+    # Eq. norm_bound lands at 1.21e-7; the printed two-digit value sits 7 %
+    # above it, so the pin allows E in (0.85, 1.04] x the quoted value.
+    E = least_misfit(7, 0.25).E
+    quoted = golden["error_bound_W7_x0_025"]["value"]
+    assert 0.85 * quoted < E <= 1.04 * quoted
+
+
+def test_layer_multipliers(golden):
+    # Section 6.1, Figure 3: at E = 1e-7, W_z = 4, 3, 2 need ~6, 27, ~500 x the
+    # layers of W_z = 7.  The layer count scales as 1/(2 z0) (Eq. N_{w'}+W).
+    def z_at(W):
+        f = lambda lz: math.log(least_misfit(W, math.exp(lz), degree=16, nx=48, n_nu=48).E) - math.log(1e-7)
+        return math.exp(brentq(f, math.log(2e-4), math.log(0.45), xtol=2e-3))
+    z7 = z_at(7)
+    for W, mult in golden["layer_multipliers_at_E_1e-7"]["value"].items():
+        ratio = z7 / z_at(int(W))
+        assert abs(ratio / mult - 1.0) < 0.15, (W, ratio, mult)
+
+
+def test_tophat_closed_form(golden):
+    # Section 6.2: top hat with h = 1/sinc.  Expanding L = 1 - exp(-2 pi i nu z)/sinc z
+    # to first order gives |L|^2 ~ (2 pi nu z)^2, so E -> (pi/3) z0 exactly as
+    # z0 -> 0; the paper's sqrt(pi/3) z0 is within 2.5 % of that.
+    for z0 in (1e-3, 1e-2):
+        E = error_bound(tophat_weights, tophat_h, 1, z0)
+        assert abs(E / z0 - math.pi / 3) < 2e-3
+        assert abs(E / z0 / golden["tophat_error_over_z0"]["value"] - 1) < 0.03
+
+
+def test_W1_least_misfit_close_to_tophat():
+    # Section 6.2: the W = 1 least-misfit curve is visually indistinguishable
+    # from the top hat, and being optimal it cannot be worse.
+    for z0 in (0.02, 0.1):
+        lm = least_misfit(1, z0)
+        Et = error_bound(tophat_weights, tophat_h, 1, z0)
+        assert lm.E <= Et * (1 + 1e-9)
+        assert lm.E > 0.9 * Et
+
+
+def test_evenness_and_h_symmetry():
+    # C is even (Section 3.2): C(s - nu) = C(-s + nu), i.e. c_i(nu) = c_{W-1-i}(-nu);
+    # h inherits the symmetry.
+    for W in (4, 7):
+        lm = least_misfit(W, 0.25)
+        nu = np.linspace(-0.5, 0.5, 11)
+        c = lm.weights(nu)
+        assert np.allclose(c, lm.weights(-nu)[:, ::-1], rtol=0, atol=1e-14)
+        x = np.linspace(0, 0.25, 7)
+        assert np.allclose(lm.h(x), lm.h(-x), rtol=1e-13)
+
+
+def test_error_decreases_with_width():
+    # Figure 8 (rms_relative_error): E falls steeply with W at x0 = 0.25.
+    Es = [least_misfit(W, 0.25).E for W in range(1, 10)]
+    assert all(b < 0.5 * a for a, b in zip(Es, Es[1:]))
+
+
+def test_fit_is_a_local_minimum():
+    # Any small change of h or of C must raise E (Eq. norm_bound is minimised).
+    lm = least_misfit(5, 0.25)
+    base = error_bound(lm.weights, lm.h, 5, 0.25)
+    for eps in (1e-4, -1e-4):
+        bumped_h = lambda x, e=eps: lm.h(x) * (1 + e * (x / 0.25) ** 2)
+        assert error_bound(lm.weights, bumped_h, 5, 0.25) > base
+        bumped_c = lambda nu, e=eps: lm.weights(nu) * (1 + e * np.array([1, 0, 0, 0, 1.0]))
+        assert error_bound(bumped_c, lm.h, 5, 0.25) > base
+
+
+def test_map_error_integrates_to_E():
+    # l(x) of Section 3.3 integrates to E^2 over [-x0, x0] / (2 x0).
+    lm = least_misfit(6, 0.25)
+    from oracle.lmfit import gauss_legendre
+    xq, wx = gauss_legendre(120, -0.25, 0.25)
+    ell = map_error(lm.weights, lm.h, 6, xq)
+    assert abs(math.sqrt((wx * ell).sum() / 0.5) / lm.E - 1) < 1e-6
