@@ -1,0 +1,428 @@
+#!/usr/bin/env python3
+"""Throughput of the improved W-stacking grid + degrid path on one GB300.
+
+Metric: visibilities per second through ``ws_degrid`` AND ``ws_grid`` (one
+unit = one visibility degridded from the model image and gridded back into a
+dirty image), W = 7, x0 = 0.25, on the survey-scale workload: a 2048 x 2048
+image over l, m in +-0.25 (FFT grid 4096 x 4096, ~490 w-planes) and 9,987,840
+visibilities from 256 antennas in a 10 km disc on 8 h tracks at declination
+-30.  Inputs are seeded synthetic data (``paper_2101_11172_gb300.synth``).
+
+One step = ws_degrid(model image) + ws_grid(visibilities) with inputs already
+in HBM; ``value`` = M x ranks / (max over ranks of the step time).  ``e2e``
+repeats the step from pinned host buffers, copies included.  The per-stage
+device times come from the library's own CUDA events (WS_FLAG_TIMING) on the
+launching stream inside the timed region.
+
+``--impl reference`` times the FP64 CPU oracle (the method written step by
+step from the paper, numpy + plain C) on a bounded slab of the same workload.
+
+Multi-GPU: every rank runs an independent replica of the workload (different
+observations need no exchange); there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "visibilities/sec grid+degrid at W=7,x0=0.25 (err vs DFT), % HBM roofline"
+UNIT = "vis/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["survey", "tiny"], default="survey")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    return ap.parse_args()
+
+
+def load_workload(name: str):
+    from paper_2101_11172_gb300 import synth
+    if name == "tiny":
+        return synth.tiny("A")
+    return synth.survey()
+
+
+def workload_config(wl, extra=None):
+    cfg = {"workload": wl.name, "image": wl.N, "grid": None, "W": wl.W, "x0": wl.x0,
+           "fov_rad": wl.fov, "visibilities": wl.M, "w_range": [round(x, 3) for x in wl.w_range],
+           "l2": "inputs larger than L2 (w-stack and visibility arrays far above 129 MB)"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# -- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                        rows.append(parts)
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        smax = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower().startswith("active")})
+        loaded = [s for s in sm if s >= 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# -- roofline ------------------------------------------------------------------
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int, launches: int):
+    """Algorithmic bytes of one launch of a stage (each item read or written once).
+
+    Every stage is averaged over its launches; with one plane chunk (the
+    survey workload fits) each stage launches once per call.
+    """
+    c8 = 8
+    plane = Np * Np * c8
+    chunks = max(1, launches)
+    if stage == "grid3d":           # write every stack cell once + read each visibility record once
+        return total_planes * plane / chunks + M * 32 / chunks
+    if stage == "screen":           # read the cropped N x N of each plane, z, correction, write the image
+        return Nw * N * N * c8 / chunks + N * N * (8 + 4 + 8)
+    if stage == "prescreen":        # write every padded plane once, read corrected image and z
+        return total_planes * plane / chunks + N * N * 16
+    if stage == "degrid3d":         # read each visibility record, write each visibility
+        return M * (32 + 8) / chunks
+    if stage in ("fft_inv", "fft_fwd"):   # one read + one write of each plane
+        return 2 * total_planes * plane / launches
+    if stage == "prep":             # uvw (24 B) + vis (8 B) in, 32 B record out
+        return M * (24 + 8 + 32)
+    if stage == "correct":
+        return N * N * (8 + 4 + 8)
+    return None
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if the source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        src = os.path.join(ROOT, "paper_2101_11172_gb300", "csrc", "wstack.cu")
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        ent = data.get(kernel)
+        if ent and ent.get("source_sha256") == sha:
+            return ent.get("dram_bytes_per_launch_full")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+# -- the oracle on a bounded slab ---------------------------------------------------
+
+def oracle_slab(wl, slab_planes: int = 9):
+    """Time the FP64 oracle (grid + degrid) on a slab of w-planes of the workload.
+
+    Sample: the slab of ``slab_planes`` consecutive w-planes in the middle of
+    the plan's range, and every visibility whose W x W x W footprint lies in
+    it.  The oracle's cost is per plane (an N' x N' FFT, the crop and screen)
+    plus per visibility; the full job is extrapolated as the slab time x
+    (planes / slab planes), with the slab's visibility count scaled the same
+    way, and reported as visibilities per second.
+    """
+    import numpy as np
+
+    from oracle import wstack as ows
+    from oracle.geometry import make_geometry, first_tap
+    from oracle.lmfit import least_misfit
+
+    g_full = make_geometry(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range)
+    lm = least_misfit(wl.W, g_full.x0)
+    mid = (g_full.t_lo + g_full.t_hi) // 2
+    t_a = mid - slab_planes // 2
+    t0 = first_tap(wl.uvw[:, 2] * g_full.nscale, wl.W)[0]
+    sel = np.nonzero((t0 >= t_a) & (t0 + wl.W - 1 <= t_a + slab_planes - 1))[0]
+    uvw, vis = wl.uvw[sel], wl.vis[sel]
+    # same nscale/n0 (they depend on fov and x0 only); t-range = the slab
+    w_lo = (t_a + wl.W / 2.0 - 0.5) / g_full.nscale      # first tap of w_lo is t_a
+    w_hi = (t_a + slab_planes - 1 - wl.W / 2.0 + 0.5) / g_full.nscale
+    g = make_geometry(wl.N, wl.x0, wl.W, wl.fov, w_lo, w_hi)
+    assert (g.t_lo, g.t_hi) == (t_a, t_a + slab_planes - 1), (g.t_lo, g.t_hi, t_a)
+    t = time.perf_counter()
+    ows.degrid(g, lm, wl.image, uvw)
+    ows.grid(g, lm, uvw, vis)
+    dt = time.perf_counter() - t
+    scale = g_full.Nw / g.Nw
+    est_total = dt * scale
+    value = wl.M / est_total
+    sample = (f"{g.Nw} of {g_full.Nw} w-planes (t = {g.t_lo}..{g.t_hi}) with the {len(sel)} visibilities "
+              f"whose footprints lie inside; grid+degrid took {dt:.1f} s, extrapolated x{scale:.1f} "
+              f"to the full {wl.M}-visibility job")
+    return value, sample, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = load_workload(args.workload)
+    for _ in range(args.warmup):
+        oracle_slab(wl, slab_planes=wl.W + 1)
+    vals, times, sample = [], [], ""
+    for _ in range(args.steps):
+        v, sample, dt = oracle_slab(wl, slab_planes=wl.W + 1)
+        vals.append(v)
+        times.append(dt)
+    value = len(vals) / sum(1.0 / v for v in vals)          # total vis / total extrapolated time
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, {"oracle": "FP64 numpy + C, single thread"}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -- our path -----------------------------------------------------------------
+
+def accuracy_sample(wl, v_gpu, d_gpu, n_vis=256, n_pix=32):
+    """Relative RMS error against the exact DFT on sampled outputs."""
+    import numpy as np
+
+    from oracle import dft
+    from oracle.geometry import make_geometry
+    g = make_geometry(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range)
+    rng = np.random.default_rng(1234)
+    kv = rng.choice(wl.M, n_vis, replace=False)
+    lmn = dft.pixel_lmn(g)
+    v_ref = dft.dft_degrid(wl.uvw[kv], lmn, wl.image)
+    ev = float(np.linalg.norm(v_gpu[kv] - v_ref) / np.linalg.norm(v_ref))
+    rows = rng.integers(0, wl.N, n_pix)
+    cols = rng.integers(0, wl.N, n_pix)
+    d_ref = dft.dft_grid(wl.uvw, wl.vis, dft.pixel_lmn(g, rows, cols))
+    ed = float(np.linalg.norm(d_gpu[rows, cols] - d_ref) / np.linalg.norm(d_ref))
+    return {"degrid_rel_rms_vs_dft": ev, "grid_rel_rms_vs_dft": ed, "sampled_vis": n_vis, "sampled_pixels": n_pix}
+
+
+def main():
+    args = parse_args()
+    if args.warmup < 3:
+        print("warning: --warmup raised to 3", file=sys.stderr)
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2101_11172_gb300 import WS_FLAG_TIMING, _lib
+    from paper_2101_11172_gb300.wstack import Plan
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    wl = load_workload(args.workload)
+    M = wl.M
+    plan = Plan(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range, flags=WS_FLAG_TIMING, device=dev)
+    uvw = torch.from_numpy(wl.uvw).to(dev)
+    vis = torch.from_numpy(wl.vis.astype(np.complex64)).to(dev)
+    img = torch.from_numpy(wl.image.astype(np.complex64)).to(dev)
+    vout = torch.empty(M, dtype=torch.complex64, device=dev)
+    dout = torch.empty(wl.N, wl.N, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.degrid(img, uvw, out=vout)
+        plan.grid(uvw, vis, out=dout)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if plan.last_status != _lib.WS_OK:
+        raise RuntimeError(f"ws status {plan.last_status}")
+    plan.stats(reset=True)
+
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t_wall
+        barrier()
+    ms = start.elapsed_time(stop) / args.steps
+    st = plan.stats(reset=True)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = M * world / (ms / 1e3)
+
+    # end to end: pinned host inputs -> device -> both calls -> results back to pinned host
+    h_uvw = torch.from_numpy(wl.uvw).pin_memory()
+    h_vis = torch.from_numpy(wl.vis.astype(np.complex64)).pin_memory()
+    h_img = torch.from_numpy(wl.image.astype(np.complex64)).pin_memory()
+    h_vout = torch.empty(M, dtype=torch.complex64).pin_memory()
+    h_dout = torch.empty(wl.N, wl.N, dtype=torch.complex64).pin_memory()
+    plan_e2e = plan
+    d_uvw, d_vis, d_img = torch.empty_like(uvw), torch.empty_like(vis), torch.empty_like(img)
+
+    def e2e_step():
+        d_uvw.copy_(h_uvw, non_blocking=True)
+        d_vis.copy_(h_vis, non_blocking=True)
+        d_img.copy_(h_img, non_blocking=True)
+        plan_e2e.degrid(d_img, d_uvw, out=vout)
+        plan_e2e.grid(d_uvw, d_vis, out=dout)
+        h_vout.copy_(vout, non_blocking=True)
+        h_dout.copy_(dout, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_e2e = e0.elapsed_time(e1) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    h2d = wl.uvw.nbytes + M * 8 + wl.N * wl.N * 8
+    d2h = M * 8 + wl.N * wl.N * 8
+    plan.stats(reset=True)
+
+    if rank != 0:
+        plan.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # stage breakdown and roofline of the dominant kernel of this library
+    peak, peak_src = measured_peaks()
+    total_planes = -(-plan.Nw // 8) * 8
+    stages = {}
+    for name, tot in st["stage_ms"].items():
+        n = st["stage_launches"][name]
+        if n == 0 or tot == 0:
+            continue
+        per_launch_ms = tot / n
+        b = stage_bytes(name, wl.N, plan.Np, plan.Nw, total_planes, M, n // max(1, st["calls"] // 2))
+        stages[name] = {"ms_per_step": tot / args.steps, "launches_per_step": n / args.steps,
+                        "ms_per_launch": per_launch_ms,
+                        "algorithmic_gb_per_launch": None if b is None else b / 1e9,
+                        "gbs": None if b is None else b / (per_launch_ms / 1e3) / 1e9}
+    ours = {k: v for k, v in stages.items() if k not in ("fft_inv", "fft_fwd")}
+    dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
+    d = stages[dom]
+    roof = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": None if d["gbs"] is None else d["gbs"] / peak, "peak_source": peak_src,
+            "traffic": traffic_for(dom)}
+    acc = {} if args.no_accuracy else accuracy_sample(wl, vout.cpu().numpy().astype(np.complex128),
+                                                       dout.cpu().numpy().astype(np.complex128))
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v_cpu, sample, _ = oracle_slab(wl, slab_planes=wl.W + 2)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (FP64 coordinates and phase arguments)", "data": "synthetic",
+            "config": workload_config(wl, {"grid": plan.Np, "w_planes": plan.Nw,
+                                           "planes_per_chunk": plan.planes_per_chunk,
+                                           "parallelism": f"replicas x{world}"}),
+            "e2e": {"value": M * world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+            "gpu_launches": None,
+            "roofline": roof, "stages": stages, "accuracy": acc, "clocks": clocks.summary(),
+            "cpu_baseline": cpu, "wall_s_timed": t_wall}
+    line["gpu_launches"] = int(round(sum(stages[k]["launches_per_step"] for k in ours) * args.steps))
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

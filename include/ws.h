@@ -1,0 +1,153 @@
+/* ws.h -- C ABI of the GB300 improved W-stacking gridder/degridder.
+ *
+ * Implements the hot path of Ye, Gull, Tan & Nikolic 2021, "High accuracy
+ * wide field imaging method in radio interferometry":
+ *   ws_degrid  Algorithm 6 (model image -> visibilities, 3-D degridding)
+ *   ws_grid    Algorithm 5 (visibilities -> dirty image, 3-D gridding)
+ * with least-misfit gridding functions C and corrections h (Section 3.3) in
+ * all three directions, W_x = W_y = W_z = W and x0 = y0 = z0.
+ *
+ * Normalisation.  Both operators are plain sums (no 1/M natural weighting,
+ * no 2 l_max or 4 l_max m_max factor, unnormalised FFTs), approximating
+ *   degrid: V_k    = sum_{i,j} f[i][j] exp(-2 pi i (u_k l_j + v_k m_i + w_k (n_ij - 1)))
+ *   grid:   d[i][j] = sum_k V_k    exp(+2 pi i (u_k l_j + v_k m_i + w_k (n_ij - 1)))
+ * (Eq. fourier_visibility and its adjoint), so that they are exact adjoints
+ * of each other: <ws_degrid(f), V> = <f, ws_grid(V)> under the plain complex
+ * inner products, up to FP32 rounding.  f is the sky brightness divided by n
+ * (Section 5.2); the caller applies weights and scale factors.
+ *
+ * Coordinates.  Image pixel [i][j] (row i along m, column j along l, both
+ * -N/2..N/2-1 after subtracting N/2) sits at l_j = (j - N/2) fov/N,
+ * m_i = (i - N/2) fov/N; n_ij = sqrt(1 - l^2 - m^2).  uvw are in wavelengths.
+ *
+ * Memory.  Every data pointer is DEVICE memory owned by the caller; the
+ * library never frees it.  Images are complex64 (interleaved float re, im)
+ * N x N row-major; visibilities complex64 length M; uvw double M x 3
+ * (u, v, w per row).  The plan owns its tables and workspace (device memory
+ * it allocates and frees).
+ *
+ * Streams.  Work is enqueued on the given stream (0 = legacy default
+ * stream).  Unless the plan was made with WS_FLAG_ASYNC, each call ends by
+ * waiting for its stream and reading back the count of visibilities it had
+ * to drop; WS_FLAG_ASYNC skips that wait and the count is available from
+ * ws_plan_dropped().  A plan must not be used by two calls at once.
+ *
+ * Errors.  Nothing aborts or traps.  Every function returns a ws_status;
+ * ws_last_error() returns a message for the calling thread's latest failure.
+ */
+#ifndef WS_H
+#define WS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ws_plan_s *ws_plan_t;
+typedef struct CUstream_st *ws_stream_t;   /* the same type as cudaStream_t */
+
+typedef enum {
+    WS_OK = 0,
+    WS_ERR_ARG = 1,        /* invalid argument or plan parameters */
+    WS_ERR_UV_RANGE = 2,   /* a u or v was not finite (NaN/inf); those visibilities were dropped */
+    WS_ERR_W_RANGE = 3,    /* a w fell outside the plan's [w_min, w_max]; those were dropped */
+    WS_ERR_CUDA = 4,       /* a CUDA or cuFFT call failed */
+    WS_ERR_OOM = 5,        /* device memory could not be allocated */
+    WS_ERR_TIMEOUT = 6     /* a bounded device wait gave up */
+} ws_status;
+
+enum {
+    WS_FLAG_ASYNC = 1u << 0,       /* do not wait for the stream at the end of each call */
+    WS_FLAG_NO_Z_OFFSET = 1u << 1, /* Eq. n_params_no_offset: n0 = 1, z in [-z0, 0] */
+    WS_FLAG_TIMING = 1u << 2       /* record CUDA events around every stage (see ws_plan_stats) */
+};
+
+/* Stages of one call, in execution order (Algorithm 5 / Algorithm 6 steps). */
+enum {
+    WS_STAGE_PREP = 0,      /* scale u, v, w; first taps; offsets nu; pre-phase */
+    WS_STAGE_BIN,           /* counting sort of visibilities into gridding tiles */
+    WS_STAGE_GRID3D,        /* Alg. 5 steps 2-3a: 3-D least-misfit gridding into the w-stack */
+    WS_STAGE_FFT_INV,       /* Alg. 5 step 3b: per-plane inverse 2-D FFTs (cuFFT) */
+    WS_STAGE_SCREEN,        /* Alg. 5 steps 3c-5: crop, w-screen, sum over planes, correction */
+    WS_STAGE_CORRECT,       /* Alg. 6 step 2: image x correction */
+    WS_STAGE_PRESCREEN,     /* Alg. 6 steps 3a-3b: w-screen and zero padding per plane */
+    WS_STAGE_FFT_FWD,       /* Alg. 6 step 3c: per-plane forward 2-D FFTs (cuFFT) */
+    WS_STAGE_DEGRID3D,      /* Alg. 6 steps 4-5: 3-D correlation with C, post-phase */
+    WS_NSTAGES
+};
+
+typedef struct {
+    int64_t calls;                     /* ws_grid + ws_degrid calls since the last reset */
+    int64_t kernel_launches;           /* this library's own kernel launches (cuFFT's not counted) */
+    double stage_ms[WS_NSTAGES];       /* device time per stage (WS_FLAG_TIMING plans only) */
+    int64_t stage_launches[WS_NSTAGES];/* kernel launches per stage (cuFFT executions for FFT stages) */
+} ws_stats_t;
+
+typedef struct {
+    int32_t N;             /* image side */
+    int32_t Np;            /* FFT grid side N' (multiple of 32, 7-smooth, >= N/(2 x0)) */
+    int32_t W;             /* kernel width in u, v and w */
+    int32_t Nw;            /* number of w-planes (Eq. N_{w'}+W, exact for the w-range) */
+    int32_t t_lo;          /* first plane index t (plane t sits at w = t / n_scale) */
+    int32_t planes_per_chunk;  /* planes held in device memory at once */
+    double x0;             /* effective cropping parameter N/(2 N') = y0 = z0 */
+    double n0;             /* Eq. n_params */
+    double nscale;         /* Eq. n_params */
+    double error_bound;    /* E of Eq. norm_bound for (W, x0) from the plan's own fit */
+    int64_t workspace_bytes;   /* device bytes the plan currently holds */
+} ws_plan_info_t;
+
+/* Build a plan.
+ *   N       image side, even, 16..32768
+ *   x0      image cropping parameter, 0 < x0 <= 0.5 (Section 3.3 box); N' is
+ *           rounded up, so the effective x0 = N/(2 N') <= x0
+ *   W       least-misfit kernel width, 1..12
+ *   fov     full field of view in direction cosines (l, m in [-fov/2, fov/2)),
+ *           0 < fov and (fov/2)^2 * 2 < 1
+ *   w_min, w_max  the w-range (wavelengths) every later call must respect
+ *   flags   WS_FLAG_*
+ * Fits C and h (Section 3.3), sizes the w-stack (Section 5.3), uploads the
+ * correction image h_x h_y h_z(z(x, y)) (Algorithm 5 step 5) and z(x, y)
+ * (Eq. z-on-sphere) to the current CUDA device.  Returns WS_ERR_ARG for bad
+ * parameters, WS_ERR_OOM / WS_ERR_CUDA on device failures; *out is set only on
+ * success. */
+ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov,
+                  double w_min, double w_max, uint32_t flags);
+
+/* Algorithm 6: image (device complex64 N x N, read) -> vis (device complex64
+ * M, overwritten), for uvw (device double M x 3).  M = 0 is allowed.
+ * Visibilities with w outside [w_min, w_max] or non-finite u, v are written as
+ * 0 and counted; the call then returns WS_ERR_W_RANGE / WS_ERR_UV_RANGE (after
+ * finishing all other visibilities). */
+ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_t M,
+                    void *vis, ws_stream_t stream);
+
+/* Algorithm 5: vis (device complex64 M, read) at uvw (device double M x 3) ->
+ * dirty (device complex64 N x N, overwritten).  Out-of-range visibilities are
+ * skipped and counted as for ws_degrid. */
+ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
+                  void *dirty, ws_stream_t stream);
+
+/* Visibilities dropped by the plan's latest call (waits for that call). */
+ws_status ws_plan_dropped(ws_plan_t plan, int64_t *dropped);
+
+/* Plan parameters and sizes. */
+ws_status ws_plan_info(ws_plan_t plan, ws_plan_info_t *info);
+
+/* Counters of the plan's calls since the last reset; waits for the plan's
+ * pending timed work.  reset != 0 clears them afterwards.  Stage times are
+ * zero unless the plan was made with WS_FLAG_TIMING. */
+ws_status ws_plan_stats(ws_plan_t plan, ws_stats_t *stats, int32_t reset);
+
+/* Release the plan's device memory and cuFFT plans (waits for its work). */
+ws_status ws_destroy(ws_plan_t plan);
+
+/* Message for the calling thread's latest non-WS_OK status ("" if none). */
+const char *ws_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WS_H */

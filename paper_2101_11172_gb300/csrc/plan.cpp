@@ -1,0 +1,562 @@
+// Plan construction and the C ABI entry points (host side).
+//
+// ws_plan   Section 5.3 (Eq. n_params / n_params_no_offset, Eq. N_{w'}+W),
+//           Section 5.1 (Eq. z-on-sphere), Section 3.3 (least-misfit C, h)
+// ws_grid   Algorithm 5
+// ws_degrid Algorithm 6
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "ws_internal.hpp"
+
+namespace ws {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+ws_status cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? WS_ERR_OOM : WS_ERR_CUDA;
+}
+
+namespace {
+
+bool seven_smooth(int64_t n) {
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+// Smallest multiple of 32 with no prime factor above 7 that is >= N/(2 x0).
+int64_t fft_size(int N, double x0) {
+    double need = N / (2.0 * x0);
+    int64_t n = 32 * std::max<int64_t>(1, (int64_t)std::ceil(need / 32.0 - 1e-12));
+    while (!seven_smooth(n)) n += 32;
+    return n;
+}
+
+// Device-side guard: makes the plan's device current for the call's scope.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+cudaError_t dev_alloc(T **ptr, size_t count, int64_t *bytes) {
+    *ptr = nullptr;
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+    if (e == cudaSuccess) *bytes += (int64_t)(count * sizeof(T));
+    return e;
+}
+
+void release(ws_plan_s *p) {
+    if (!p) return;
+    DeviceScope scope(p->dev >= 0 ? p->dev : 0);
+    if (p->fft_made) cufftDestroy(p->fft);
+    for (auto &t : p->pending) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    for (cudaEvent_t e : p->free_events) cudaEventDestroy(e);
+    cudaFree(p->d_wcoef);
+    cudaFree(p->d_corr);
+    cudaFree(p->d_zsplit);
+    cudaFree(p->d_stack);
+    cudaFree(p->d_rec);
+    cudaFree(p->d_list);
+    cudaFree(p->d_counts);
+    cudaFree(p->d_offsets);
+    cudaFree(p->d_blocksums);
+    cudaFree(p->d_acc);
+    cudaFree(p->d_img);
+    cudaFree(p->d_drop);
+    if (p->h_drop) cudaFreeHost(p->h_drop);
+    delete p;
+}
+
+// Grow the per-call buffers to hold M visibilities.
+ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid) {
+    if (M > p->rec_cap) {
+        cudaFree(p->d_rec);
+        p->bytes -= p->rec_cap * (int64_t)sizeof(ws::VisRec);
+        p->rec_cap = 0;
+        cudaError_t e = dev_alloc(&p->d_rec, (size_t)M, &p->bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "allocating visibility records");
+        p->rec_cap = M;
+    }
+    // gridding: at most (2 x 2 x ceil((W-1)/TT + 1)) tiles per visibility
+    const int64_t per = grid ? 4 * ((p->L.W - 1 + TT - 1) / TT + 1) : 1;
+    const int64_t need = M * per;
+    if (need > p->list_cap) {
+        cudaFree(p->d_list);
+        p->bytes -= p->list_cap * 4;
+        p->list_cap = 0;
+        cudaError_t e = dev_alloc(&p->d_list, (size_t)need, &p->bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "allocating tile lists");
+        p->list_cap = need;
+    }
+    return WS_OK;
+}
+
+cudaEvent_t take_event(ws_plan_s *p) {
+    if (!p->free_events.empty()) {
+        cudaEvent_t e = p->free_events.back();
+        p->free_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Fold completed stage events into the statistics (waits for them).
+void fold_pending(ws_plan_s *p) {
+    for (auto &t : p->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(t.stop) == cudaSuccess && cudaEventElapsedTime(&ms, t.start, t.stop) == cudaSuccess)
+            p->stats.stage_ms[t.stage] += ms;
+        p->free_events.push_back(t.start);
+        p->free_events.push_back(t.stop);
+    }
+    p->pending.clear();
+}
+
+// Times one stage on the call's stream when the plan has WS_FLAG_TIMING.
+struct StageTimer {
+    ws_plan_s *p;
+    cudaStream_t s;
+    int stage;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageTimer(ws_plan_s *p_, cudaStream_t s_, int stage_, int launches) : p(p_), s(s_), stage(stage_) {
+        p->stats.stage_launches[stage] += launches;
+        if (stage != WS_STAGE_FFT_INV && stage != WS_STAGE_FFT_FWD) p->stats.kernel_launches += launches;
+        if (!(p->flags & WS_FLAG_TIMING)) return;
+        if (p->pending.size() > 4096) fold_pending(p);
+        a = take_event(p);
+        b = take_event(p);
+        if (a && b) cudaEventRecord(a, s);
+    }
+    ~StageTimer() {
+        if (a && b) {
+            cudaEventRecord(b, s);
+            p->pending.push_back({stage, a, b});
+        } else {
+            if (a) p->free_events.push_back(a);
+            if (b) p->free_events.push_back(b);
+        }
+    }
+};
+
+ws_status finish_call(ws_plan_s *p, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(p->h_drop, p->d_drop, 2 * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the drop counters");
+    if (p->flags & WS_FLAG_ASYNC) return WS_OK;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the stream");
+    p->last_dropped = (int64_t)(p->h_drop[0] + p->h_drop[1]);
+    if (p->h_drop[0]) {
+        set_error(std::to_string(p->h_drop[0]) + " visibilities had non-finite or huge u, v and were dropped");
+        return WS_ERR_UV_RANGE;
+    }
+    if (p->h_drop[1]) {
+        set_error(std::to_string(p->h_drop[1]) + " visibilities had w outside the plan's w-range and were dropped");
+        return WS_ERR_W_RANGE;
+    }
+    return WS_OK;
+}
+
+}  // namespace
+}  // namespace ws
+
+using namespace ws;
+
+extern "C" {
+
+const char *ws_last_error(void) { return g_last_error.c_str(); }
+
+ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
+                  uint32_t flags) {
+    if (!out) {
+        set_error("ws_plan: out is NULL");
+        return WS_ERR_ARG;
+    }
+    *out = nullptr;
+    if (N < 16 || N > 32768 || N % 8) {
+        set_error("ws_plan: N must be a multiple of 8 in [16, 32768]");
+        return WS_ERR_ARG;
+    }
+    if (!(x0 > 0.0 && x0 <= 0.5)) {
+        set_error("ws_plan: need 0 < x0 <= 0.5");
+        return WS_ERR_ARG;
+    }
+    if (W < 1 || W > kMaxW) {
+        set_error("ws_plan: need 1 <= W <= 12");
+        return WS_ERR_ARG;
+    }
+    const double lmax = 0.5 * fov;
+    if (!(fov > 0.0) || !(2.0 * lmax * lmax < 1.0)) {
+        set_error("ws_plan: need fov > 0 with the map corner inside the unit circle");
+        return WS_ERR_ARG;
+    }
+    if (!std::isfinite(w_min) || !std::isfinite(w_max) || w_min > w_max) {
+        set_error("ws_plan: need finite w_min <= w_max");
+        return WS_ERR_ARG;
+    }
+    if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_TIMING)) {
+        set_error("ws_plan: unknown flag bits");
+        return WS_ERR_ARG;
+    }
+    const int64_t Np = fft_size(N, x0);
+    if (Np > 65536) {
+        set_error("ws_plan: FFT grid larger than 65536");
+        return WS_ERR_ARG;
+    }
+    ws_plan_s *p = new (std::nothrow) ws_plan_s;
+    if (!p) {
+        set_error("ws_plan: out of host memory");
+        return WS_ERR_OOM;
+    }
+    p->flags = flags;
+    p->fov = fov;
+    p->w_min = w_min;
+    p->w_max = w_max;
+    p->x0 = N / (2.0 * (double)Np);
+    // Eq. n_params: z in [-z0, z0] with z0 = x0 (or Eq. n_params_no_offset: n0 = 1)
+    const double r2 = 2.0 * lmax * lmax;
+    const double one_minus_nmin = r2 / (1.0 + std::sqrt(1.0 - r2));
+    double nscale, n0;
+    if (flags & WS_FLAG_NO_Z_OFFSET) {
+        nscale = one_minus_nmin / p->x0;
+        n0 = 1.0;
+    } else {
+        nscale = one_minus_nmin / (2.0 * p->x0);
+        n0 = 1.0 - p->x0 * nscale;
+    }
+    // planes: first tap of w'_min to last tap of w'_max (Section 3.3 tap rule)
+    const long long t_lo = (long long)std::floor(nscale * w_min + 0.5 * W) - (W - 1);
+    const long long t_hi = (long long)std::floor(nscale * w_max + 0.5 * W);
+    if (t_lo < -2040 || t_hi > 2040 - TT) {
+        set_error("ws_plan: w-range needs more than ~4000 w-planes (plane index |t| must stay below 2040)");
+        delete p;
+        return WS_ERR_ARG;
+    }
+    Launch &L = p->L;
+    L.N = N;
+    L.Np = (int)Np;
+    L.W = W;
+    L.t_lo = (int)t_lo;
+    L.Nw = (int)(t_hi - t_lo + 1);
+    L.ntu = (int)(Np / TU);
+    L.ntv = (int)(Np / TV);
+    L.ntt = (L.Nw + TT - 1) / TT;
+    L.uv_scale = Np * (fov / N);
+    L.nscale = nscale;
+    L.n0m1 = n0 - 1.0;
+    p->ntiles = (int64_t)L.ntu * L.ntv * L.ntt;
+    if (p->ntiles + 1 > (int64_t)4096 * 4096) {
+        set_error("ws_plan: too many gridding tiles (N' x N' x planes too large)");
+        delete p;
+        return WS_ERR_ARG;
+    }
+
+    std::string err;
+    if (!fit_least_misfit(W, p->x0, &p->fit, &err)) {
+        set_error("ws_plan: " + err);
+        delete p;
+        return WS_ERR_ARG;
+    }
+    std::vector<double> mono;
+    monomial_weights(p->fit, 1e-10, kMaxDeg, &p->wdeg, &mono);
+    p->wcoef_host.assign(mono.begin(), mono.end());
+
+    // correction image h(x_j) h(y_i) h(z_ij) and the split z_ij (Eq. z-on-sphere)
+    const double dl = fov / N;
+    std::vector<double> hx(N);
+    for (int j = 0; j < N; ++j) hx[j] = h_series(p->fit, (j - N / 2) / (double)Np);
+    std::vector<float> corr((size_t)N * N);
+    std::vector<float2> zs((size_t)N * N);
+    for (int i = 0; i < N; ++i) {
+        const double m = (i - N / 2) * dl;
+        for (int j = 0; j < N; ++j) {
+            const double l = (j - N / 2) * dl;
+            const double rr = l * l + m * m;
+            const double nm1 = -rr / (1.0 + std::sqrt(1.0 - rr));
+            double z = (nm1 + (1.0 - n0)) / nscale;
+            z = std::min(std::max(z, -p->x0), p->x0);
+            corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * h_series(p->fit, z));
+            const double hi = std::nearbyint(z * 8192.0) / 8192.0;
+            zs[(size_t)i * N + j] = make_float2((float)hi, (float)(z - hi));
+        }
+    }
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        ws_status st = cuda_fail(e, "ws_plan: no CUDA device");
+        delete p;
+        return st;
+    }
+    p->dev = dev;
+    const size_t plane_bytes = (size_t)Np * Np * sizeof(float2);
+    // planes per chunk: all planes if they fit the budget, else a multiple of TT
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t budget = (size_t)(0.6 * (double)free_b);
+    if (const char *env = std::getenv("WS_STACK_BYTES")) budget = (size_t)std::strtoull(env, nullptr, 10);
+    int P = L.ntt * TT;
+    if (const char *env = std::getenv("WS_PLANES_PER_CHUNK")) {
+        int want = std::atoi(env);
+        if (want > 0) P = std::min(P, std::max(TT, (want / TT) * TT));
+    }
+    const int fit_planes = (int)std::min<size_t>(budget / plane_bytes, (size_t)1 << 20);
+    if (fit_planes < P) P = std::max(TT, (fit_planes / TT) * TT);
+    p->P = P;
+
+    ws_status st = WS_OK;
+    const char *what = nullptr;
+#define WS_TRY(call, msg)              \
+    do {                               \
+        e = (call);                    \
+        if (e != cudaSuccess) {        \
+            what = msg;                \
+            goto fail;                 \
+        }                              \
+    } while (0)
+    WS_TRY(dev_alloc(&p->d_wcoef, p->wcoef_host.size(), &p->bytes), "allocating weight table");
+    WS_TRY(cudaMemcpy(p->d_wcoef, p->wcoef_host.data(), p->wcoef_host.size() * sizeof(float),
+                      cudaMemcpyHostToDevice), "uploading weight table");
+    WS_TRY(dev_alloc(&p->d_corr, corr.size(), &p->bytes), "allocating correction image");
+    WS_TRY(cudaMemcpy(p->d_corr, corr.data(), corr.size() * sizeof(float), cudaMemcpyHostToDevice),
+           "uploading correction image");
+    WS_TRY(dev_alloc(&p->d_zsplit, zs.size(), &p->bytes), "allocating z table");
+    WS_TRY(cudaMemcpy(p->d_zsplit, zs.data(), zs.size() * sizeof(float2), cudaMemcpyHostToDevice),
+           "uploading z table");
+    WS_TRY(dev_alloc(&p->d_stack, (size_t)P * Np * Np, &p->bytes), "allocating the w-stack chunk");
+    WS_TRY(dev_alloc(&p->d_counts, (size_t)p->ntiles + 1, &p->bytes), "allocating tile counts");
+    WS_TRY(dev_alloc(&p->d_offsets, (size_t)p->ntiles + 1, &p->bytes), "allocating tile offsets");
+    WS_TRY(dev_alloc(&p->d_blocksums, (size_t)4096, &p->bytes), "allocating scan sums");
+    WS_TRY(dev_alloc(&p->d_acc, (size_t)N * N, &p->bytes), "allocating the accumulator");
+    WS_TRY(dev_alloc(&p->d_img, (size_t)N * N, &p->bytes), "allocating the corrected image");
+    WS_TRY(dev_alloc(&p->d_drop, (size_t)2, &p->bytes), "allocating drop counters");
+    WS_TRY(cudaMallocHost((void **)&p->h_drop, 2 * sizeof(unsigned long long)), "allocating pinned counters");
+    std::memset(p->h_drop, 0, 2 * sizeof(unsigned long long));
+#undef WS_TRY
+    {
+        int n[2] = {(int)Np, (int)Np};
+        p->fft_batch = TT;
+        cufftResult r = cufftPlanMany(&p->fft, 2, n, nullptr, 1, (int)(Np * Np), nullptr, 1, (int)(Np * Np),
+                                      CUFFT_C2C, p->fft_batch);
+        if (r != CUFFT_SUCCESS) {
+            set_error("ws_plan: cufftPlanMany failed with code " + std::to_string((int)r));
+            release(p);
+            return r == CUFFT_ALLOC_FAILED ? WS_ERR_OOM : WS_ERR_CUDA;
+        }
+        p->fft_made = true;
+        size_t ws_bytes = 0;
+        if (cufftGetSize(p->fft, &ws_bytes) == CUFFT_SUCCESS) p->bytes += (int64_t)ws_bytes;
+    }
+    *out = p;
+    return WS_OK;
+fail:
+    st = cuda_fail(e, what);
+    release(p);
+    return st;
+}
+
+static ws_status run_ffts(ws_plan_s *p, int planes, int direction, cudaStream_t s) {
+    if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) {
+        set_error("cufftSetStream failed");
+        return WS_ERR_CUDA;
+    }
+    const size_t plane = (size_t)p->L.Np * p->L.Np;
+    for (int q = 0; q < planes; q += p->fft_batch) {
+        cufftComplex *ptr = reinterpret_cast<cufftComplex *>(p->d_stack + q * plane);
+        cufftResult r = cufftExecC2C(p->fft, ptr, ptr, direction);
+        if (r != CUFFT_SUCCESS) {
+            set_error("cufftExecC2C failed with code " + std::to_string((int)r));
+            return WS_ERR_CUDA;
+        }
+    }
+    return WS_OK;
+}
+
+ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M, void *dirty,
+                  ws_stream_t stream) {
+    if (!plan || M < 0 || !dirty || (M > 0 && (!uvw || !vis)) || M > ((int64_t)1 << 31) / 12) {
+        set_error("ws_grid: invalid argument");
+        return WS_ERR_ARG;
+    }
+    ws_plan_s *p = plan;
+    DeviceScope scope(p->dev);
+    if (!scope.ok) {
+        set_error("ws_grid: cannot select the plan's device");
+        return WS_ERR_CUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), true);
+    if (st != WS_OK) return st;
+    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "ws_grid: clearing counters");
+    p->stats.calls += 1;
+    {
+        StageTimer t(p, s, WS_STAGE_PREP, M > 0 ? 1 : 0);
+        if ((e = launch_prep(p, uvw, static_cast<const float2 *>(vis), M, true, s)) != cudaSuccess)
+            return cuda_fail(e, "ws_grid: prep kernel");
+    }
+    {
+        StageTimer t(p, s, WS_STAGE_BIN, M > 0 ? 5 : 3);
+        if ((e = launch_bin(p, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: binning kernels");
+    }
+    const int total = p->L.ntt * TT;
+    const int nchunks = (total + p->P - 1) / p->P;
+    for (int c = 0; c < nchunks; ++c) {
+        const int planes = std::min(p->P, total - c * p->P);
+        {
+            StageTimer t(p, s, WS_STAGE_GRID3D, 1);
+            if ((e = launch_grid_chunk(p, c, planes, s)) != cudaSuccess)
+                return cuda_fail(e, "ws_grid: grid3d kernel");
+        }
+        {
+            StageTimer t(p, s, WS_STAGE_FFT_INV, (planes + p->fft_batch - 1) / p->fft_batch);
+            if ((st = run_ffts(p, planes, CUFFT_INVERSE, s)) != WS_OK) return st;
+        }
+        {
+            StageTimer t(p, s, WS_STAGE_SCREEN, 1);
+            if ((e = launch_screen_accum(p, c, planes, c == 0, c == nchunks - 1, static_cast<float2 *>(dirty),
+                                         s)) != cudaSuccess)
+                return cuda_fail(e, "ws_grid: screen kernel");
+        }
+    }
+    return finish_call(p, s);
+}
+
+ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_t M, void *vis,
+                    ws_stream_t stream) {
+    if (!plan || M < 0 || !image || (M > 0 && (!uvw || !vis)) || M > ((int64_t)1 << 31) / 12) {
+        set_error("ws_degrid: invalid argument");
+        return WS_ERR_ARG;
+    }
+    ws_plan_s *p = plan;
+    DeviceScope scope(p->dev);
+    if (!scope.ok) {
+        set_error("ws_degrid: cannot select the plan's device");
+        return WS_ERR_CUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), false);
+    if (st != WS_OK) return st;
+    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "ws_degrid: clearing counters");
+    if (M == 0) return finish_call(p, s);
+    if ((e = cudaMemsetAsync(vis, 0, (size_t)M * sizeof(float2), s)) != cudaSuccess)
+        return cuda_fail(e, "ws_degrid: clearing the output");
+    p->stats.calls += 1;
+    {
+        StageTimer t(p, s, WS_STAGE_PREP, 1);
+        if ((e = launch_prep(p, uvw, nullptr, M, false, s)) != cudaSuccess)
+            return cuda_fail(e, "ws_degrid: prep kernel");
+    }
+    {
+        StageTimer t(p, s, WS_STAGE_BIN, 5);
+        if ((e = launch_bin(p, M, false, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: binning kernels");
+    }
+    {
+        StageTimer t(p, s, WS_STAGE_CORRECT, 1);
+        if ((e = launch_correct_image(p, static_cast<const float2 *>(image), s)) != cudaSuccess)
+            return cuda_fail(e, "ws_degrid: correction kernel");
+    }
+    const int total = p->L.ntt * TT;
+    const int nchunks = (total + p->P - 1) / p->P;
+    for (int c = 0; c < nchunks; ++c) {
+        const int planes = std::min(p->P, total - c * p->P);
+        {
+            StageTimer t(p, s, WS_STAGE_PRESCREEN, 1);
+            if ((e = launch_prescreen(p, c, planes, s)) != cudaSuccess)
+                return cuda_fail(e, "ws_degrid: prescreen kernel");
+        }
+        {
+            StageTimer t(p, s, WS_STAGE_FFT_FWD, (planes + p->fft_batch - 1) / p->fft_batch);
+            if ((st = run_ffts(p, planes, CUFFT_FORWARD, s)) != WS_OK) return st;
+        }
+        {
+            StageTimer t(p, s, WS_STAGE_DEGRID3D, 1);
+            if ((e = launch_degrid_chunk(p, c, planes, M, static_cast<float2 *>(vis), s)) != cudaSuccess)
+                return cuda_fail(e, "ws_degrid: degrid3d kernel");
+        }
+    }
+    return finish_call(p, s);
+}
+
+ws_status ws_plan_dropped(ws_plan_t plan, int64_t *dropped) {
+    if (!plan || !dropped) {
+        set_error("ws_plan_dropped: invalid argument");
+        return WS_ERR_ARG;
+    }
+    DeviceScope scope(plan->dev);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "ws_plan_dropped: synchronize");
+    plan->last_dropped = (int64_t)(plan->h_drop[0] + plan->h_drop[1]);
+    *dropped = plan->last_dropped;
+    return WS_OK;
+}
+
+ws_status ws_plan_stats(ws_plan_t plan, ws_stats_t *stats, int32_t reset) {
+    if (!plan || !stats) {
+        set_error("ws_plan_stats: invalid argument");
+        return WS_ERR_ARG;
+    }
+    DeviceScope scope(plan->dev);
+    fold_pending(plan);
+    *stats = plan->stats;
+    if (reset) plan->stats = ws_stats_t{};
+    return WS_OK;
+}
+
+ws_status ws_plan_info(ws_plan_t plan, ws_plan_info_t *info) {
+    if (!plan || !info) {
+        set_error("ws_plan_info: invalid argument");
+        return WS_ERR_ARG;
+    }
+    info->N = plan->L.N;
+    info->Np = plan->L.Np;
+    info->W = plan->L.W;
+    info->Nw = plan->L.Nw;
+    info->t_lo = plan->L.t_lo;
+    info->planes_per_chunk = plan->P;
+    info->x0 = plan->x0;
+    info->n0 = plan->L.n0m1 + 1.0;
+    info->nscale = plan->L.nscale;
+    info->error_bound = plan->fit.E;
+    info->workspace_bytes = plan->bytes;
+    return WS_OK;
+}
+
+ws_status ws_destroy(ws_plan_t plan) {
+    if (!plan) return WS_OK;
+    {
+        DeviceScope scope(plan->dev);
+        cudaDeviceSynchronize();
+    }
+    release(plan);
+    return WS_OK;
+}
+
+}  // extern "C"

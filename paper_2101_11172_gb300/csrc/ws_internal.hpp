@@ -1,0 +1,111 @@
+// Internal definitions shared by the plan (host) and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ws.h"
+#include "lmfit.hpp"
+
+namespace ws {
+
+// Gridding tile owned by one CTA of the gridding kernel: TT w-planes x TV
+// grid rows (v) x TU grid columns (u).  N' is a multiple of 32, so TU and TV
+// divide it; the plane count is padded to a multiple of TT.
+constexpr int TU = 32;
+constexpr int TV = 16;
+constexpr int TT = 8;
+constexpr int kMaxW = 12;
+constexpr int kMaxDeg = 16;
+
+// One visibility after pre-processing: first grid point of its W x W x W
+// footprint (u and v wrapped into [0, N'), t relative to the plan's t_lo;
+// t0 < 0 marks a dropped visibility), the three offsets nu in [-1/2, 1/2)
+// and a complex value (gridding: V exp(2 pi i w (n0 - 1)); degridding:
+// exp(-2 pi i w (n0 - 1))).
+struct __align__(16) VisRec {
+    int32_t r0, s0, t0;
+    float nux, nuy, nuz;
+    float vre, vim;
+};
+
+struct DeviceTables {
+    const float *wcoef;    // W x (deg+1) monomial coefficients of c_i(nu) in nu
+    int W, deg;
+};
+
+struct Launch {            // geometry the kernels need
+    int N, Np, W, Nw, t_lo;
+    int ntu, ntv, ntt;     // tile counts along u, v, t
+    double uv_scale;       // u' = u * uv_scale (= N' * dl)
+    double nscale, n0m1;   // w' = w * nscale; n0 - 1
+};
+
+}  // namespace ws
+
+struct ws_plan_s {
+    int dev = -1;
+    uint32_t flags = 0;
+    ws::Launch L{};
+    double x0 = 0.0, fov = 0.0, w_min = 0.0, w_max = 0.0;
+    ws::LeastMisfitFit fit;
+    int wdeg = 0;
+    std::vector<float> wcoef_host;
+
+    // device tables (plan lifetime)
+    float *d_wcoef = nullptr;      // W x (wdeg+1)
+    float *d_corr = nullptr;       // N x N: h(x_j) h(y_i) h(z_ij)
+    float2 *d_zsplit = nullptr;    // N x N: z = hi + lo, hi a multiple of 2^-13
+    // stack workspace
+    int P = 0;                     // planes per chunk (multiple of TT)
+    float2 *d_stack = nullptr;     // P x N' x N'
+    int fft_batch = 0;
+    cufftHandle fft = 0;           // batch fft_batch
+    bool fft_made = false;
+    // per-call buffers (grow on demand)
+    ws::VisRec *d_rec = nullptr;
+    int64_t rec_cap = 0;
+    uint32_t *d_list = nullptr;
+    int64_t list_cap = 0;
+    uint32_t *d_counts = nullptr;  // ntiles + 1
+    uint32_t *d_offsets = nullptr; // ntiles + 1
+    uint32_t *d_blocksums = nullptr;
+    int64_t ntiles = 0;
+    float4 *d_acc = nullptr;       // N x N: (sum re, sum im, comp re, comp im)
+    float2 *d_img = nullptr;       // N x N: corrected image (degridding)
+    unsigned long long *d_drop = nullptr;   // [0] = non-finite uv, [1] = w out of range
+    unsigned long long *h_drop = nullptr;   // pinned mirror
+    int64_t last_dropped = 0;
+    int64_t bytes = 0;
+    // statistics (WS_FLAG_TIMING adds CUDA events around each stage)
+    ws_stats_t stats{};
+    struct Timed {
+        int stage;
+        cudaEvent_t start, stop;
+    };
+    std::vector<Timed> pending;           // recorded, not yet folded into stats
+    std::vector<cudaEvent_t> free_events;
+};
+
+namespace ws {
+
+void set_error(const std::string &msg);
+ws_status cuda_fail(cudaError_t e, const char *what);
+
+// Launchers (wstack.cu).
+cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,
+                        bool grid, cudaStream_t s);
+cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
+cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
+cudaError_t launch_screen_accum(const ws_plan_s *p, int chunk, int planes, bool first, bool last,
+                                float2 *dirty, cudaStream_t s);
+cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s);
+cudaError_t launch_prescreen(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
+cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64_t M,
+                                float2 *vis, cudaStream_t s);
+
+}  // namespace ws

@@ -1,0 +1,532 @@
+// CUDA kernels of the improved W-stacking hot path (sm_103a).
+//
+// Gridding (Algorithm 5):   prep -> bin -> per plane chunk: grid3d -> inverse FFT (cuFFT)
+//                           -> screen_accum (crop, x exp(2 pi i t z), sum over t, x h_x h_y h_z)
+// Degridding (Algorithm 6): prep -> bin -> correct_image (x h_x h_y h_z) -> per plane chunk:
+//                           prescreen (x exp(-2 pi i t z), zero pad) -> forward FFT (cuFFT)
+//                           -> degrid3d (3-D correlation with C_x C_y C_z, x exp(-2 pi i w (n0-1)))
+//
+// Grid layout: plane p of a chunk holds N' x N' complex64 values, row s
+// (v direction) major, column r (u direction) minor, both stored modulo N'.
+// Because exp(2 pi i r j / N') is N'-periodic in r, a tap that runs past the
+// grid edge wraps onto the opposite edge and the inverse DFT of the wrapped
+// grid is exactly the sum over all integers r of Eq. gridded-dirty-map; the
+// centred crop |x| < x0 is then rows/columns [N'-N/2, N') and [0, N/2).
+#include <math.h>
+
+#include "ws_internal.hpp"
+
+namespace ws {
+namespace {
+
+__device__ __forceinline__ int wrap_add(int a, int b, int n) {
+    int s = a + b;
+    return s >= n ? s - n : s;
+}
+
+// c_i(nu) by Horner's rule on the monomial table (FP32).
+__device__ __forceinline__ float tap_weight(const float *__restrict__ coef, int deg, int i, float nu) {
+    const float *c = coef + i * (deg + 1);
+    float acc = __ldg(c + deg);
+    for (int m = deg - 1; m >= 0; --m) acc = fmaf(acc, nu, __ldg(c + m));
+    return acc;
+}
+
+// Lane l < 3W of a warp writes weight (axis l / W, tap l % W) of record r.
+__device__ __forceinline__ void warp_weights(const float *__restrict__ coef, int deg, int W,
+                                             const VisRec &r, int lane, float *swt) {
+    if (lane < 3 * W) {
+        int axis = lane / W;
+        int i = lane - axis * W;
+        float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
+        swt[lane] = tap_weight(coef, deg, i, nu);
+    }
+    __syncwarp();
+}
+
+// exp(2 pi i t z) with z = hi + lo split so that t * hi is exact in FP32
+// (hi is a multiple of 2^-13 of magnitude <= 1/2 and |t| < 2^11): the phase in
+// turns is frac(t hi) + t lo, reduced exactly before the single rounding.
+__device__ __forceinline__ void phase_tz(float t, float2 z, float *s, float *c) {
+    float hi = t * z.x;
+    float turns = fmaf(t, z.y, hi - rintf(hi));
+    sincospif(2.0f * turns, s, c);
+}
+
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
+    float y = v - comp;
+    float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// ---------------------------------------------------------------------------
+// Pre-processing (Section 3.3 tap rule, Section 5.2 scaling and pre-phase)
+// ---------------------------------------------------------------------------
+__global__ void prep_kernel(Launch L, const double *__restrict__ uvw, const float2 *__restrict__ vis,
+                            int64_t M, int grid, VisRec *__restrict__ rec,
+                            unsigned long long *__restrict__ drop) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    const double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
+    const int W = L.W;
+    VisRec r;
+    r.r0 = r.s0 = 0;
+    r.t0 = -1;
+    r.nux = r.nuy = r.nuz = 0.f;
+    r.vre = r.vim = 0.f;
+    const double up = u * L.uv_scale, vp = v * L.uv_scale, wp = w * L.nscale;
+    if (!(fabs(up) < 1e15) || !(fabs(vp) < 1e15)) {   // also catches NaN
+        atomicAdd(&drop[0], 1ull);
+        rec[k] = r;
+        return;
+    }
+    const double ft = floor(wp + 0.5 * W);
+    const double t0 = ft - (W - 1) - L.t_lo;
+    if (!(t0 >= 0.0 && t0 + W <= (double)L.Nw)) {      // NaN w fails too
+        atomicAdd(&drop[1], 1ull);
+        rec[k] = r;
+        return;
+    }
+    const double fu = floor(up + 0.5 * W), fv = floor(vp + 0.5 * W);
+    const double ru = fu - (W - 1), rv = fv - (W - 1);
+    const double Np = (double)L.Np;
+    double mu = fmod(ru, Np), mv = fmod(rv, Np);     // exact for integer-valued doubles
+    if (mu < 0.0) mu += Np;
+    if (mv < 0.0) mv += Np;
+    r.r0 = (int)mu;
+    r.s0 = (int)mv;
+    r.t0 = (int)t0;
+    r.nux = (float)(up + 0.5 * (W - 1) - fu);
+    r.nuy = (float)(vp + 0.5 * (W - 1) - fv);
+    r.nuz = (float)(wp + 0.5 * (W - 1) - ft);
+    // pre-phase exp(+2 pi i w (n0 - 1)), argument reduced in FP64
+    double turns = w * L.n0m1;
+    turns -= rint(turns);
+    float s, c;
+    sincospif(2.0f * (float)turns, &s, &c);
+    if (grid) {
+        const float2 V = vis[k];
+        r.vre = V.x * c - V.y * s;
+        r.vim = V.x * s + V.y * c;
+    } else {
+        r.vre = c;          // conjugate phase applied after degridding
+        r.vim = -s;
+    }
+    rec[k] = r;
+}
+
+// ---------------------------------------------------------------------------
+// Binning: counting sort of (visibility, tile) pairs by tile id
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tile_id(const Launch &L, int tt, int tv, int tu) {
+    return ((uint32_t)tt * L.ntv + tv) * L.ntu + tu;
+}
+
+// Tiles of the gridding footprint (grid) or the tile of the first tap (degrid).
+template <bool GRID>
+__device__ __forceinline__ int record_keys(const Launch &L, const VisRec &r, uint32_t *keys) {
+    if (r.t0 < 0) return 0;
+    if (!GRID) {
+        keys[0] = tile_id(L, r.t0 / TT, r.s0 / TV, r.r0 / TU);
+        return 1;
+    }
+    int tu[2], tv[2];
+    tu[0] = r.r0 / TU;
+    int tu_last = wrap_add(r.r0, L.W - 1, L.Np) / TU;
+    int nu_ = tu_last != tu[0] ? 2 : 1;
+    tu[1] = tu_last;
+    tv[0] = r.s0 / TV;
+    int tv_last = wrap_add(r.s0, L.W - 1, L.Np) / TV;
+    int nv_ = tv_last != tv[0] ? 2 : 1;
+    tv[1] = tv_last;
+    int tt0 = r.t0 / TT, tt1 = (r.t0 + L.W - 1) / TT;
+    int n = 0;
+    for (int tt = tt0; tt <= tt1; ++tt)
+        for (int b = 0; b < nv_; ++b)
+            for (int a = 0; a < nu_; ++a) keys[n++] = tile_id(L, tt, tv[b], tu[a]);
+    return n;
+}
+
+constexpr int kMaxKeys = 2 * 2 * 3;
+
+template <bool GRID>
+__global__ void count_kernel(Launch L, const VisRec *__restrict__ rec, int64_t M,
+                             uint32_t *__restrict__ counts) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    uint32_t keys[kMaxKeys];
+    int n = record_keys<GRID>(L, rec[k], keys);
+    for (int i = 0; i < n; ++i) atomicAdd(&counts[keys[i]], 1u);
+}
+
+template <bool GRID>
+__global__ void scatter_kernel(Launch L, const VisRec *__restrict__ rec, int64_t M,
+                               const uint32_t *__restrict__ offsets, uint32_t *__restrict__ fill,
+                               uint32_t *__restrict__ list) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    uint32_t keys[kMaxKeys];
+    int n = record_keys<GRID>(L, rec[k], keys);
+    for (int i = 0; i < n; ++i) list[offsets[keys[i]] + atomicAdd(&fill[keys[i]], 1u)] = (uint32_t)k;
+}
+
+// Exclusive scan of n uint32 (n <= 4096 * 4096): per-block scan of 4096
+// elements, scan of the block sums in one block, then add back.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerBlock = 4 * kScanThreads;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = warp_sums[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    uint32_t before = (wid ? warp_sums[wid - 1] : 0u) + x - v;
+    *total = warp_sums[31];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_block_kernel(const uint32_t *__restrict__ in,
+                                                                  uint32_t *__restrict__ out,
+                                                                  uint32_t *__restrict__ sums, int64_t n) {
+    const int64_t base = (int64_t)blockIdx.x * kScanPerBlock + 4 * threadIdx.x;
+    uint32_t a[4];
+    for (int i = 0; i < 4; ++i) a[i] = base + i < n ? in[base + i] : 0u;
+    uint32_t local = a[0] + a[1] + a[2] + a[3], total;
+    uint32_t run = block_exclusive_scan(local, &total);
+    for (int i = 0; i < 4; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += a[i];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_sums_kernel(uint32_t *sums, int nb) {
+    const int base = 4 * threadIdx.x;
+    uint32_t a[4];
+    for (int i = 0; i < 4; ++i) a[i] = base + i < nb ? sums[base + i] : 0u;
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(a[0] + a[1] + a[2] + a[3], &total);
+    for (int i = 0; i < 4; ++i) {
+        if (base + i < nb) sums[base + i] = run;
+        run += a[i];
+    }
+}
+
+__global__ void scan_add_kernel(uint32_t *__restrict__ out, const uint32_t *__restrict__ sums, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += sums[i / kScanPerBlock];
+}
+
+// ---------------------------------------------------------------------------
+// Gridding: Algorithm 5 steps 2 and 3a (Eq. gridded_vis).  One CTA owns one
+// TT x TV x TU tile of the stack chunk, accumulates every (visibility, tile)
+// pair of its list in shared memory and writes the tile exactly once.
+// ---------------------------------------------------------------------------
+constexpr int kGridThreads = 256;
+constexpr int kTileCells = TT * TV * TU;
+
+__global__ void __launch_bounds__(kGridThreads)
+grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
+              const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
+              uint32_t tile_base, int chunk_tt0, float2 *__restrict__ stack) {
+    __shared__ float sre[kTileCells];
+    __shared__ float sim[kTileCells];
+    __shared__ float swt[kGridThreads / 32][3 * kMaxW];
+    const uint32_t tile = tile_base + blockIdx.x;
+    const int tu = tile % L.ntu;
+    const int tv = (tile / L.ntu) % L.ntv;
+    const int tt = tile / (L.ntu * L.ntv);
+    for (int i = threadIdx.x; i < kTileCells; i += kGridThreads) {
+        sre[i] = 0.f;
+        sim[i] = 0.f;
+    }
+    __syncthreads();
+    const int W = L.W, Np = L.Np;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t beg = offsets[tile], end = offsets[tile + 1];
+    const int u_org = tu * TU, v_org = tv * TV, t_org = tt * TT;
+    float *wt = swt[warp];
+    for (uint32_t e = beg + warp; e < end; e += kGridThreads / 32) {
+        const VisRec r = rec[list[e]];
+        warp_weights(coef, deg, W, r, lane, wt);
+        for (int pair = lane; pair < W * W; pair += 32) {
+            const int a = pair % W, b = pair / W;
+            const int lc = wrap_add(r.r0, a, Np) - u_org;
+            const int lr = wrap_add(r.s0, b, Np) - v_org;
+            if (lc < 0 || lc >= TU || lr < 0 || lr >= TV) continue;
+            const float wxy = wt[a] * wt[W + b];
+            const float vr = r.vre * wxy, vi = r.vim * wxy;
+            for (int c = 0; c < W; ++c) {
+                const int pl = r.t0 + c - t_org;
+                if (pl < 0 || pl >= TT) continue;
+                const float wz = wt[2 * W + c];
+                const int idx = (pl * TV + lr) * TU + lc;
+                atomicAdd(&sre[idx], vr * wz);
+                atomicAdd(&sim[idx], vi * wz);
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    const size_t plane = (size_t)Np * Np;
+    const int p0 = t_org - chunk_tt0 * TT;
+    for (int i = threadIdx.x; i < kTileCells / 2; i += kGridThreads) {
+        const int cell = 2 * i;
+        const int lc = cell % TU, lr = (cell / TU) % TV, pl = cell / (TU * TV);
+        float4 v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
+        float2 *dst = stack + (size_t)(p0 + pl) * plane + (size_t)(v_org + lr) * Np + u_org + lc;
+        *reinterpret_cast<float4 *>(dst) = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 5 steps 3c-5: crop, x exp(2 pi i t z(x, y)), sum over t (Kahan),
+// and on the last chunk x h_x(x) h_y(y) h_z(z(x, y)).  One thread per pair
+// of adjacent pixels, looping over the chunk's planes.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+screen_accum_kernel(Launch L, const float2 *__restrict__ stack, int plane0, int planes,
+                    const float2 *__restrict__ zsplit, const float *__restrict__ corr,
+                    float4 *__restrict__ acc, int first, int last, float2 *__restrict__ dirty) {
+    const int N = L.N, Np = L.Np, half = N / 2;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)N * half) return;
+    const int ii = (int)(q / half), jj = (int)(q % half) * 2;
+    const int prow = ii < half ? ii - half + Np : ii - half;
+    const int pcol = jj < half ? jj - half + Np : jj - half;
+    const int64_t pix = (int64_t)ii * N + jj;
+    const float2 z0 = zsplit[pix], z1 = zsplit[pix + 1];
+    float4 s0, s1;                 // (sum re, sum im, comp re, comp im) of the two pixels
+    if (first) {
+        s0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        s1 = s0;
+    } else {
+        s0 = acc[pix];
+        s1 = acc[pix + 1];
+    }
+    const size_t plane = (size_t)Np * Np;
+    const float4 *src = reinterpret_cast<const float4 *>(stack + (size_t)prow * Np + pcol);
+    const int nvalid = min(planes, L.Nw - plane0);
+#pragma unroll 4
+    for (int p = 0; p < nvalid; ++p) {
+        const float4 v = __ldcs(src + p * (plane / 2));
+        const float t = (float)(plane0 + p + L.t_lo);
+        float sn, cs;
+        phase_tz(t, z0, &sn, &cs);
+        kahan_add(s0.x, s0.z, v.x * cs - v.y * sn);
+        kahan_add(s0.y, s0.w, v.x * sn + v.y * cs);
+        phase_tz(t, z1, &sn, &cs);
+        kahan_add(s1.x, s1.z, v.z * cs - v.w * sn);
+        kahan_add(s1.y, s1.w, v.z * sn + v.w * cs);
+    }
+    if (last) {
+        const float h0 = corr[pix], h1 = corr[pix + 1];
+        *reinterpret_cast<float4 *>(dirty + pix) =
+            make_float4(h0 * (s0.x - s0.z), h0 * (s0.y - s0.w), h1 * (s1.x - s1.z), h1 * (s1.y - s1.w));
+    } else {
+        acc[pix] = s0;
+        acc[pix + 1] = s1;
+    }
+}
+
+// Algorithm 6 step 2: image x h_x h_y h_z.
+__global__ void correct_image_kernel(int64_t n, const float *__restrict__ corr,
+                                     const float2 *__restrict__ image, float2 *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float h = corr[i];
+    const float2 f = image[i];
+    out[i] = make_float2(h * f.x, h * f.y);
+}
+
+// Algorithm 6 steps 3a-3b: x exp(-2 pi i t z(x, y)) and zero padding to
+// N' x N', for every plane of the chunk.  One thread per two adjacent grid
+// cells of a row, looping over planes.
+__global__ void __launch_bounds__(256)
+prescreen_kernel(Launch L, const float2 *__restrict__ img, const float2 *__restrict__ zsplit,
+                 int plane0, int planes, float2 *__restrict__ stack) {
+    const int N = L.N, Np = L.Np, half = N / 2;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)Np * (Np / 2)) return;
+    const int R = (int)(q / (Np / 2)), C = (int)(q % (Np / 2)) * 2;
+    const size_t plane = (size_t)Np * Np;
+    float4 *dst = reinterpret_cast<float4 *>(stack + (size_t)R * Np + C);
+    const bool rin = R < half || R >= Np - half;
+    const bool cin = C < half || C >= Np - half;     // C even and N/2 even: both cells agree
+    if (!(rin && cin)) {
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int p = 0; p < planes; ++p) __stcs(dst + p * (plane / 2), zero);
+        return;
+    }
+    const int ii = R < half ? R + half : R - (Np - half);
+    const int jj = C < half ? C + half : C - (Np - half);
+    const int64_t pix = (int64_t)ii * N + jj;
+    const float2 g0 = img[pix], g1 = img[pix + 1];
+    const float2 z0 = zsplit[pix], z1 = zsplit[pix + 1];
+#pragma unroll 4
+    for (int p = 0; p < planes; ++p) {
+        const float t = (float)(plane0 + p + L.t_lo);
+        float sn, cs;
+        float4 o;
+        phase_tz(t, z0, &sn, &cs);            // multiply by exp(-i phi) = cs - i sn
+        o.x = g0.x * cs + g0.y * sn;
+        o.y = g0.y * cs - g0.x * sn;
+        phase_tz(t, z1, &sn, &cs);
+        o.z = g1.x * cs + g1.y * sn;
+        o.w = g1.y * cs - g1.x * sn;
+        __stcs(dst + p * (plane / 2), o);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Degridding: Algorithm 6 steps 4-5.  One warp per visibility (visiting them
+// in tile order for cache reuse); lane <-> (row b, plane c) pair of the
+// footprint, W contiguous columns per lane, then a warp reduction.  Each
+// chunk adds its planes' share to vis in chunk order.
+// ---------------------------------------------------------------------------
+constexpr int kDegridThreads = 256;
+
+__global__ void __launch_bounds__(kDegridThreads)
+degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
+                const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_order,
+                const float2 *__restrict__ stack, int plane0, int planes, float2 *__restrict__ vis) {
+    __shared__ float swt[kDegridThreads / 32][3 * kMaxW];
+    const int64_t widx = ((int64_t)blockIdx.x * kDegridThreads + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (widx >= (int64_t)*n_order) return;      // entries of the sorted list (dropped ones excluded)
+    const uint32_t k = order[widx];
+    const VisRec r = rec[k];
+    if (r.t0 < 0) return;
+    const int W = L.W, Np = L.Np;
+    const int c_lo = max(0, plane0 - r.t0);
+    const int c_hi = min(W - 1, plane0 + planes - 1 - r.t0);
+    if (c_lo > c_hi) return;
+    float *wt = swt[warp];
+    warp_weights(coef, deg, W, r, lane, wt);
+    float ar = 0.f, ai = 0.f;
+    const size_t plane = (size_t)Np * Np;
+    for (int pair = lane; pair < W * W; pair += 32) {
+        const int b = pair % W, c = pair / W;
+        if (c < c_lo || c > c_hi) continue;
+        const float2 *row = stack + (size_t)(r.t0 + c - plane0) * plane + (size_t)wrap_add(r.s0, b, Np) * Np;
+        float sr = 0.f, si = 0.f;
+        int col = r.r0;
+        for (int a = 0; a < W; ++a) {
+            const float2 f = __ldg(row + col);
+            const float wa = wt[a];
+            sr = fmaf(wa, f.x, sr);
+            si = fmaf(wa, f.y, si);
+            col = col + 1 == Np ? 0 : col + 1;
+        }
+        const float wbc = wt[W + b] * wt[2 * W + c];
+        ar = fmaf(wbc, sr, ar);
+        ai = fmaf(wbc, si, ai);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ar += __shfl_xor_sync(0xffffffffu, ar, o);
+        ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) {
+        float2 out = vis[k];
+        out.x += ar * r.vre - ai * r.vim;
+        out.y += ar * r.vim + ai * r.vre;
+        vis[k] = out;
+    }
+}
+
+inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, bool grid,
+                        cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    prep_kernel<<<blocks_for(M, 256), 256, 0, s>>>(p->L, uvw, vis, M, grid ? 1 : 0, p->d_rec, p->d_drop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s) {
+    const int64_t n = p->ntiles + 1;
+    cudaError_t e = cudaMemsetAsync(p->d_counts, 0, n * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    if (M > 0 && grid)
+        count_kernel<true><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts);
+    else if (M > 0)
+        count_kernel<false><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts);
+    const int nb = (int)((n + kScanPerBlock - 1) / kScanPerBlock);
+    scan_block_kernel<<<nb, kScanThreads, 0, s>>>(p->d_counts, p->d_offsets, p->d_blocksums, n);
+    scan_sums_kernel<<<1, kScanThreads, 0, s>>>(p->d_blocksums, nb);
+    scan_add_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p->d_offsets, p->d_blocksums, n);
+    e = cudaMemsetAsync(p->d_counts, 0, n * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    if (M == 0) return cudaGetLastError();
+    if (grid)
+        scatter_kernel<true><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_offsets, p->d_counts,
+                                                               p->d_list);
+    else
+        scatter_kernel<false><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_offsets,
+                                                                p->d_counts, p->d_list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
+    const int tiles_per_tt = p->L.ntu * p->L.ntv;
+    const int chunk_tt0 = chunk * (p->P / TT);
+    const uint32_t tile_base = (uint32_t)chunk_tt0 * tiles_per_tt;
+    const unsigned nblocks = (unsigned)(planes / TT) * tiles_per_tt;
+    grid3d_kernel<<<nblocks, kGridThreads, 0, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list,
+                                                  tile_base, chunk_tt0, p->d_stack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_screen_accum(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
+                                cudaStream_t s) {
+    const int64_t n = (int64_t)p->L.N * (p->L.N / 2);
+    screen_accum_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p->L, p->d_stack, chunk * p->P, planes, p->d_zsplit,
+                                                          p->d_corr, p->d_acc, first ? 1 : 0, last ? 1 : 0,
+                                                          dirty);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s) {
+    const int64_t n = (int64_t)p->L.N * p->L.N;
+    correct_image_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, p->d_corr, image, p->d_img);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prescreen(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
+    const int64_t n = (int64_t)p->L.Np * (p->L.Np / 2);
+    prescreen_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p->L, p->d_img, p->d_zsplit, chunk * p->P, planes,
+                                                       p->d_stack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64_t M, float2 *vis,
+                                cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    degrid3d_kernel<<<blocks_for(M * 32, kDegridThreads), kDegridThreads, 0, s>>>(
+        p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_list, p->d_offsets + p->ntiles, p->d_stack, chunk * p->P,
+        planes, vis);
+    return cudaGetLastError();
+}
+
+}  // namespace ws

@@ -1,0 +1,95 @@
+"""PyTorch-facing wrapper of the C ABI: device tensors in, device tensors out.
+
+Only marshalling happens here (shapes, dtypes, pointers, the current CUDA
+stream); the computation is the CUDA library's.  Tensors must already live on
+the plan's device: complex64 images (N, N) with rows along m and columns along
+l, complex64 visibilities (M,), float64 uvw (M, 3) in wavelengths.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+
+class Plan:
+    """Improved W-stacking plan (``ws_plan``); see ``include/ws.h``."""
+
+    def __init__(self, N: int, x0: float, W: int, fov: float, w_min: float, w_max: float,
+                 flags: int = 0, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        with torch.cuda.device(self.device):
+            self.handle = _lib.ws_plan(int(N), float(x0), int(W), float(fov), float(w_min),
+                                       float(w_max), int(flags))
+        info = _lib.ws_plan_info(self.handle)
+        self.N, self.Np, self.W, self.Nw = info.N, info.Np, info.W, info.Nw
+        self.t_lo, self.planes_per_chunk = info.t_lo, info.planes_per_chunk
+        self.x0, self.n0, self.nscale = info.x0, info.n0, info.nscale
+        self.error_bound = info.error_bound
+        self.flags = flags
+        self.last_status = _lib.WS_OK
+
+    @property
+    def workspace_bytes(self) -> int:
+        return _lib.ws_plan_info(self.handle).workspace_bytes
+
+    def _stream(self, stream):
+        s = torch.cuda.current_stream(self.device) if stream is None else stream
+        return s.cuda_stream
+
+    def _check(self, t: torch.Tensor, dtype, shape, name):
+        if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous() \
+                or t.device != self.device:
+            raise ValueError(f"{name}: need contiguous {dtype} {tuple(shape)} on {self.device}, "
+                             f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+
+    def degrid(self, image: torch.Tensor, uvw: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+        """Algorithm 6: model image -> visibilities (``ws_degrid``)."""
+        M = uvw.shape[0]
+        self._check(image, torch.complex64, (self.N, self.N), "image")
+        self._check(uvw, torch.float64, (M, 3), "uvw")
+        if out is None:
+            out = torch.empty(M, dtype=torch.complex64, device=self.device)
+        self._check(out, torch.complex64, (M,), "out")
+        self.last_status = _lib.ws_degrid(self.handle, image.data_ptr(), uvw.data_ptr(), M,
+                                          out.data_ptr(), self._stream(stream))
+        return out
+
+    def grid(self, uvw: torch.Tensor, vis: torch.Tensor, out: torch.Tensor | None = None,
+             stream=None) -> torch.Tensor:
+        """Algorithm 5: visibilities -> dirty image (``ws_grid``)."""
+        M = uvw.shape[0]
+        self._check(uvw, torch.float64, (M, 3), "uvw")
+        self._check(vis, torch.complex64, (M,), "vis")
+        if out is None:
+            out = torch.empty(self.N, self.N, dtype=torch.complex64, device=self.device)
+        self._check(out, torch.complex64, (self.N, self.N), "out")
+        self.last_status = _lib.ws_grid(self.handle, uvw.data_ptr(), vis.data_ptr(), M,
+                                        out.data_ptr(), self._stream(stream))
+        return out
+
+    def stats(self, reset: bool = False) -> dict:
+        """Call counters and (WS_FLAG_TIMING plans) per-stage device milliseconds."""
+        return _lib.ws_plan_stats(self.handle, reset).as_dict()
+
+    def dropped(self) -> int:
+        return _lib.ws_plan_dropped(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.ws_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
