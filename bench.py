@@ -139,27 +139,30 @@ def measured_peaks():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int, launches: int):
-    """Algorithmic bytes of one launch of a stage (each item read or written once).
+def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int, nchunks: int,
+                fft_batch: int = 8):
+    """Algorithmic bytes of ONE launch of a stage: each item read or written once.
 
-    Every stage is averaged over its launches; with one plane chunk (the
-    survey workload fits) each stage launches once per call.
+    Per call the gridding direction moves M x 32 B of records into the tiles
+    and writes every stack cell once (grid3d), and the screen reads the
+    N x N crop of every plane; degridding writes every padded plane once
+    (prescreen) and reads back one record and writes one visibility per
+    visibility (degrid3d).  A plane transform reads and writes its plane once.
+    Stages that run once per plane chunk divide by the chunk count.
     """
-    c8 = 8
-    plane = Np * Np * c8
-    chunks = max(1, launches)
-    if stage == "grid3d":           # write every stack cell once + read each visibility record once
-        return total_planes * plane / chunks + M * 32 / chunks
-    if stage == "screen":           # read the cropped N x N of each plane, z, correction, write the image
-        return Nw * N * N * c8 / chunks + N * N * (8 + 4 + 8)
-    if stage == "prescreen":        # write every padded plane once, read corrected image and z
-        return total_planes * plane / chunks + N * N * 16
-    if stage == "degrid3d":         # read each visibility record, write each visibility
-        return M * (32 + 8) / chunks
-    if stage in ("fft_inv", "fft_fwd"):   # one read + one write of each plane
-        return 2 * total_planes * plane / launches
-    if stage == "prep":             # uvw (24 B) + vis (8 B) in, 32 B record out
-        return M * (24 + 8 + 32)
+    plane = Np * Np * 8
+    if stage == "grid3d":
+        return (total_planes * plane + M * 32) / nchunks
+    if stage == "screen":
+        return (Nw * N * N * 8) / nchunks + N * N * (8 + 4 + 8)
+    if stage == "prescreen":
+        return (total_planes * plane) / nchunks + N * N * 16
+    if stage == "degrid3d":
+        return M * (32 + 8) / nchunks
+    if stage in ("fft_inv", "fft_fwd"):
+        return 2 * fft_batch * plane
+    if stage == "prep":
+        return M * (24 + 4 + 32)
     if stage == "correct":
         return N * N * (8 + 4 + 8)
     return None
@@ -183,45 +186,71 @@ def traffic_for(kernel: str):
 
 # -- the oracle on a bounded slab ---------------------------------------------------
 
-def oracle_slab(wl, slab_planes: int = 9):
-    """Time the FP64 oracle (grid + degrid) on a slab of w-planes of the workload.
-
-    Sample: the slab of ``slab_planes`` consecutive w-planes in the middle of
-    the plan's range, and every visibility whose W x W x W footprint lies in
-    it.  The oracle's cost is per plane (an N' x N' FFT, the crop and screen)
-    plus per visibility; the full job is extrapolated as the slab time x
-    (planes / slab planes), with the slab's visibility count scaled the same
-    way, and reported as visibilities per second.
-    """
+def _oracle_slab_run(wl, g_full, lm, t_a, n_vis, rng):
+    """Oracle grid + degrid over the W planes t_a .. t_a+W-1 for n_vis visibilities
+    whose footprints start at plane t_a; returns (seconds, visibilities used)."""
     import numpy as np
 
     from oracle import wstack as ows
-    from oracle.geometry import make_geometry, first_tap
-    from oracle.lmfit import least_misfit
-
-    g_full = make_geometry(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range)
-    lm = least_misfit(wl.W, g_full.x0)
-    mid = (g_full.t_lo + g_full.t_hi) // 2
-    t_a = mid - slab_planes // 2
+    from oracle.geometry import first_tap, make_geometry
     t0 = first_tap(wl.uvw[:, 2] * g_full.nscale, wl.W)[0]
-    sel = np.nonzero((t0 >= t_a) & (t0 + wl.W - 1 <= t_a + slab_planes - 1))[0]
-    uvw, vis = wl.uvw[sel], wl.vis[sel]
-    # same nscale/n0 (they depend on fov and x0 only); t-range = the slab
-    w_lo = (t_a + wl.W / 2.0 - 0.5) / g_full.nscale      # first tap of w_lo is t_a
-    w_hi = (t_a + slab_planes - 1 - wl.W / 2.0 + 0.5) / g_full.nscale
-    g = make_geometry(wl.N, wl.x0, wl.W, wl.fov, w_lo, w_hi)
-    assert (g.t_lo, g.t_hi) == (t_a, t_a + slab_planes - 1), (g.t_lo, g.t_hi, t_a)
+    pool = np.nonzero(t0 == t_a)[0]
+    sel = rng.choice(pool, min(n_vis, pool.size), replace=False)
+    w_lo = (t_a + wl.W / 2.0 - 0.5) / g_full.nscale          # first tap of w_lo is t_a
+    g = make_geometry(wl.N, wl.x0, wl.W, wl.fov, w_lo, w_lo)
+    assert (g.t_lo, g.t_hi) == (t_a, t_a + wl.W - 1)
     t = time.perf_counter()
-    ows.degrid(g, lm, wl.image, uvw)
-    ows.grid(g, lm, uvw, vis)
-    dt = time.perf_counter() - t
-    scale = g_full.Nw / g.Nw
-    est_total = dt * scale
-    value = wl.M / est_total
-    sample = (f"{g.Nw} of {g_full.Nw} w-planes (t = {g.t_lo}..{g.t_hi}) with the {len(sel)} visibilities "
-              f"whose footprints lie inside; grid+degrid took {dt:.1f} s, extrapolated x{scale:.1f} "
-              f"to the full {wl.M}-visibility job")
-    return value, sample, dt
+    ows.degrid(g, lm, wl.image, wl.uvw[sel])
+    ows.grid(g, lm, wl.uvw[sel], wl.vis[sel])
+    return time.perf_counter() - t, sel.size
+
+
+class OracleRate:
+    """Throughput of the FP64 oracle (grid + degrid) on a bounded sample of the workload.
+
+    The oracle's work is one N' x N' transform, crop and screen per w-plane
+    and one W^3 spread / gather per visibility, so its time for the full job
+    is ``planes x c_plane + M x c_vis``.  Both rates are measured on the
+    minimal slab of W planes in the middle of the w-range: ``calibrate`` runs
+    it with a small and a larger set of visibilities whose footprints lie in
+    the slab (c_vis from the difference); ``step`` re-times the small run and
+    returns the extrapolated visibilities per second.
+    """
+
+    def __init__(self, wl, m_small=1000, m_large=5000):
+        import numpy as np
+
+        from oracle.geometry import make_geometry
+        from oracle.lmfit import least_misfit
+        self.wl = wl
+        self.g = make_geometry(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range)
+        self.lm = least_misfit(wl.W, self.g.x0)
+        self.t_a = (self.g.t_lo + self.g.t_hi) // 2 - wl.W // 2
+        self.m_small, self.m_large = m_small, m_large
+        self.rng = np.random.default_rng(77)
+        self.c_vis = None
+        from oracle import wstack as ows
+        ows.correction(self.g, self.lm)      # the per-image product is plan work: made once, outside the timing
+
+    def calibrate(self):
+        t_s, n_s = _oracle_slab_run(self.wl, self.g, self.lm, self.t_a, self.m_small, self.rng)
+        t_l, n_l = _oracle_slab_run(self.wl, self.g, self.lm, self.t_a, self.m_large, self.rng)
+        self.c_vis = max(0.0, (t_l - t_s) / max(1, n_l - n_s))
+        return t_s + t_l
+
+    def step(self):
+        t_s, n_s = _oracle_slab_run(self.wl, self.g, self.lm, self.t_a, self.m_small, self.rng)
+        c_plane = max(0.0, (t_s - n_s * self.c_vis) / self.wl.W)
+        total = self.g.Nw * c_plane + self.wl.M * self.c_vis
+        self.last = (t_s, c_plane)
+        return self.wl.M / total, t_s
+
+    def sample(self):
+        t_s, c_plane = self.last
+        return (f"slab of {self.wl.W} of {self.g.Nw} w-planes (t = {self.t_a}..{self.t_a + self.wl.W - 1}) with "
+                f"{self.m_small} and {self.m_large} visibilities starting there: {c_plane:.2f} s per plane, "
+                f"{1e3 * self.c_vis:.3f} ms per visibility (grid + degrid), extrapolated to "
+                f"{self.g.Nw} planes and {self.wl.M} visibilities")
 
 
 def run_reference(args):
@@ -229,19 +258,21 @@ def run_reference(args):
     if rank != 0:
         return 0
     wl = load_workload(args.workload)
-    for _ in range(args.warmup):
-        oracle_slab(wl, slab_planes=wl.W + 1)
-    vals, times, sample = [], [], ""
+    rate = OracleRate(wl)
+    rate.calibrate()                                  # part of the warm-up
+    for _ in range(max(0, args.warmup - 2)):
+        rate.step()
+    vals, times = [], []
     for _ in range(args.steps):
-        v, sample, dt = oracle_slab(wl, slab_planes=wl.W + 1)
+        v, dt = rate.step()
         vals.append(v)
         times.append(dt)
-    value = len(vals) / sum(1.0 / v for v in vals)          # total vis / total extrapolated time
+    value = len(vals) / sum(1.0 / v for v in vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl.M / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(wl, {"oracle": "FP64 numpy + C, single thread"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": rate.sample()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -384,13 +415,14 @@ def main():
     # stage breakdown and roofline of the dominant kernel of this library
     peak, peak_src = measured_peaks()
     total_planes = -(-plan.Nw // 8) * 8
+    nchunks = -(-total_planes // plan.planes_per_chunk)
     stages = {}
     for name, tot in st["stage_ms"].items():
         n = st["stage_launches"][name]
         if n == 0 or tot == 0:
             continue
         per_launch_ms = tot / n
-        b = stage_bytes(name, wl.N, plan.Np, plan.Nw, total_planes, M, n // max(1, st["calls"] // 2))
+        b = stage_bytes(name, wl.N, plan.Np, plan.Nw, total_planes, M, nchunks)
         stages[name] = {"ms_per_step": tot / args.steps, "launches_per_step": n / args.steps,
                         "ms_per_launch": per_launch_ms,
                         "algorithmic_gb_per_launch": None if b is None else b / 1e9,
@@ -405,8 +437,10 @@ def main():
                                                        dout.cpu().numpy().astype(np.complex128))
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v_cpu, sample, _ = oracle_slab(wl, slab_planes=wl.W + 2)
-        cpu = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        rate = OracleRate(wl)
+        rate.calibrate()
+        v_cpu, _ = rate.step()
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": rate.sample()}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 (FP64 coordinates and phase arguments)", "data": "synthetic",

@@ -100,6 +100,36 @@ class LeastMisfit:
         return out.reshape(x.shape)
 
 
+def interpolated_h(lm: "LeastMisfit", n_table: int = 4097, order: int = 10):
+    """h on [-x0, x0] by the paper's own recipe (Section 5.3): a table of h on a
+    uniform grid and polynomial interpolation of high degree within it.
+
+    The table holds the exact h-step values at ``n_table`` uniform points; each
+    argument is interpolated by the Lagrange polynomial through the ``order``
+    table points nearest to it.  Returns a callable.
+    """
+    x0 = lm.x0
+    xs = np.linspace(-x0, x0, n_table)
+    hs = lm.h(xs)
+    step = xs[1] - xs[0]
+
+    def h_of(x):
+        x = np.asarray(x, dtype=np.float64)
+        flat = np.clip(x.reshape(-1), -x0, x0)
+        first = np.clip(np.floor((flat + x0) / step).astype(np.int64) - order // 2 + 1, 0, n_table - order)
+        out = np.zeros_like(flat)
+        for a in range(order):
+            xa = xs[first + a]
+            basis = np.ones_like(flat)
+            for b in range(order):
+                if b != a:
+                    basis *= (flat - xs[first + b]) / (xa - xs[first + b])
+            out += hs[first + a] * basis
+        return out.reshape(x.shape)
+
+    return h_of
+
+
 def misfit_L(weights_fn, h_fn, W, x, nu):
     """L(x, nu) of Eq. csum2 on the outer grid x (nx,) by nu (nn,)."""
     s = tap_offsets(W)

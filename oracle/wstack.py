@@ -23,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 from .geometry import Geometry, first_tap
-from .lmfit import LeastMisfit
+from .lmfit import LeastMisfit, interpolated_h
 
 
 # -- one dimension: Algorithms 1 and 2 --------------------------------------
@@ -74,13 +74,27 @@ def prephase(geom: Geometry, w):
     return np.exp(2j * np.pi * turns)
 
 
+_CORRECTIONS = {}
+
+
 def correction(geom: Geometry, lm: LeastMisfit, with_hz: bool = True):
-    """h_x(x) h_y(y) h_z(z(x, y)) on the N x N image (Algorithm 5 step 5)."""
-    hx = lm.h(geom.pixel_x())
-    out = hx[None, :] * hx[:, None]
-    if with_hz:
-        out = out * lm.h(geom.pixel_z())
-    return out
+    """h_x(x) h_y(y) h_z(z(x, y)) on the N x N image (Algorithm 5 step 5).
+
+    Section 5.3: the product is computed once for all image points, with
+    h_z(z) taken by high-degree interpolation in a uniform table of h.  It
+    depends on the image geometry only (not on the w-range), so it is kept
+    per geometry.
+    """
+    key = (geom.N, geom.Np, geom.x0, geom.fov, geom.nscale, geom.n0, lm.W, lm.x0, lm.beta.tobytes(), with_hz)
+    if key not in _CORRECTIONS:
+        hx = lm.h(geom.pixel_x())
+        out = hx[None, :] * hx[:, None]
+        if with_hz:
+            out = out * interpolated_h(lm)(geom.pixel_z())
+        if len(_CORRECTIONS) > 8:
+            _CORRECTIONS.clear()
+        _CORRECTIONS[key] = out
+    return _CORRECTIONS[key]
 
 
 def _crop_index(geom: Geometry):

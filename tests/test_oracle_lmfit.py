@@ -85,3 +85,15 @@ def test_map_error_integrates_to_E():
     xq, wx = gauss_legendre(120, -0.25, 0.25)
     ell = map_error(lm.weights, lm.h, 6, xq)
     assert abs(math.sqrt((wx * ell).sum() / 0.5) / lm.E - 1) < 1e-6
+
+
+def test_table_interpolation_of_h_matches_direct_formula():
+    # Section 5.3: h_z(z) off any grid by high-degree interpolation within a
+    # uniform table of h; for the smooth least-misfit h this is exact to rounding.
+    from oracle.lmfit import interpolated_h
+    for W, x0 in ((7, 0.25), (4, 0.3), (5, 0.3657)):
+        lm = least_misfit(W, x0)
+        f = interpolated_h(lm)
+        x = np.random.default_rng(W).uniform(-x0, x0, 500)
+        x[:2] = [-x0, x0]
+        assert np.abs(f(x) - lm.h(x)).max() < 1e-13 * np.abs(lm.h(x)).max()
