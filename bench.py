@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["survey", "tiny"], default="survey")
+    ap.add_argument("--workload", choices=["survey", "tiny", "profile"], default="survey")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -58,6 +58,8 @@ def load_workload(name: str):
     from paper_2101_11172_gb300 import synth
     if name == "tiny":
         return synth.tiny("A")
+    if name == "profile":
+        return synth.survey_slab()
     return synth.survey()
 
 
@@ -139,28 +141,32 @@ def measured_peaks():
         return 6800.0, "fallback 6.8 TB/s"
 
 
-def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int, nchunks: int,
-                fft_batch: int = 8):
-    """Algorithmic bytes of ONE launch of a stage: each item read or written once.
+def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int, nchunks: int):
+    """Algorithmic bytes of ONE launch of a stage: what that kernel must move.
 
-    Per call the gridding direction moves M x 32 B of records into the tiles
-    and writes every stack cell once (grid3d), and the screen reads the
-    N x N crop of every plane; degridding writes every padded plane once
-    (prescreen) and reads back one record and writes one visibility per
-    visibility (degrid3d).  A plane transform reads and writes its plane once.
-    Stages that run once per plane chunk divide by the chunk count.
+    Per plane, gridding writes the full N' x N' plane once (grid3d); the
+    column transform reads it and writes back the N crop rows (cols_inv);
+    the row transform reads those rows and, once per chunk, the running sum
+    (rows_inv).  Degridding mirrors it: the row transform reads the image and
+    z and writes N rows (rows_fwd); the column transform reads them and writes
+    the full plane (cols_fwd).  Records are 32 B per visibility.  Stages that
+    run once per plane chunk divide by the chunk count.
     """
-    plane = Np * Np * 8
+    c8 = 8
+    full, crop = Np * Np * c8, N * Np * c8
+    planes = total_planes / nchunks
     if stage == "grid3d":
-        return (total_planes * plane + M * 32) / nchunks
-    if stage == "screen":
-        return (Nw * N * N * 8) / nchunks + N * N * (8 + 4 + 8)
-    if stage == "prescreen":
-        return (total_planes * plane) / nchunks + N * N * 16
+        return planes * full + M * 32 / nchunks
+    if stage == "cols_inv":
+        return planes * (full + crop)
+    if stage == "rows_inv":
+        return planes * crop + N * N * (8 + 16 + 16 + 4 + 8)
+    if stage == "rows_fwd":
+        return planes * (N * N * 16 + crop)
+    if stage == "cols_fwd":
+        return planes * (crop + full)
     if stage == "degrid3d":
         return M * (32 + 8) / nchunks
-    if stage in ("fft_inv", "fft_fwd"):
-        return 2 * fft_batch * plane
     if stage == "prep":
         return M * (24 + 4 + 32)
     if stage == "correct":
@@ -427,7 +433,7 @@ def main():
                         "ms_per_launch": per_launch_ms,
                         "algorithmic_gb_per_launch": None if b is None else b / 1e9,
                         "gbs": None if b is None else b / (per_launch_ms / 1e3) / 1e9}
-    ours = {k: v for k, v in stages.items() if k not in ("fft_inv", "fft_fwd")}
+    ours = stages
     dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
     d = stages[dom]
     roof = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": peak, "unit": "GB/s",

@@ -52,7 +52,7 @@ typedef enum {
     WS_ERR_ARG = 1,        /* invalid argument or plan parameters */
     WS_ERR_UV_RANGE = 2,   /* a u or v was not finite (NaN/inf); those visibilities were dropped */
     WS_ERR_W_RANGE = 3,    /* a w fell outside the plan's [w_min, w_max]; those were dropped */
-    WS_ERR_CUDA = 4,       /* a CUDA or cuFFT call failed */
+    WS_ERR_CUDA = 4,       /* a CUDA call failed */
     WS_ERR_OOM = 5,        /* device memory could not be allocated */
     WS_ERR_TIMEOUT = 6     /* a bounded device wait gave up */
 } ws_status;
@@ -68,20 +68,21 @@ enum {
     WS_STAGE_PREP = 0,      /* scale u, v, w; first taps; offsets nu; pre-phase */
     WS_STAGE_BIN,           /* counting sort of visibilities into gridding tiles */
     WS_STAGE_GRID3D,        /* Alg. 5 steps 2-3a: 3-D least-misfit gridding into the w-stack */
-    WS_STAGE_FFT_INV,       /* Alg. 5 step 3b: per-plane inverse 2-D FFTs (cuFFT) */
-    WS_STAGE_SCREEN,        /* Alg. 5 steps 3c-5: crop, w-screen, sum over planes, correction */
+    WS_STAGE_COLS_INV,      /* Alg. 5 steps 3b-3c, first half: inverse DFT along v, crop rows */
+    WS_STAGE_ROWS_INV,      /* Alg. 5 steps 3b-5, second half: inverse DFT along u, crop,
+                               w-screen, sum over planes, correction */
     WS_STAGE_CORRECT,       /* Alg. 6 step 2: image x correction */
-    WS_STAGE_PRESCREEN,     /* Alg. 6 steps 3a-3b: w-screen and zero padding per plane */
-    WS_STAGE_FFT_FWD,       /* Alg. 6 step 3c: per-plane forward 2-D FFTs (cuFFT) */
+    WS_STAGE_ROWS_FWD,      /* Alg. 6 steps 3a-3c, first half: w-screen, zero pad, DFT along l */
+    WS_STAGE_COLS_FWD,      /* Alg. 6 step 3c, second half: zero pad, DFT along m */
     WS_STAGE_DEGRID3D,      /* Alg. 6 steps 4-5: 3-D correlation with C, post-phase */
     WS_NSTAGES
 };
 
 typedef struct {
     int64_t calls;                     /* ws_grid + ws_degrid calls since the last reset */
-    int64_t kernel_launches;           /* this library's own kernel launches (cuFFT's not counted) */
+    int64_t kernel_launches;           /* kernel launches of the counted calls */
     double stage_ms[WS_NSTAGES];       /* device time per stage (WS_FLAG_TIMING plans only) */
-    int64_t stage_launches[WS_NSTAGES];/* kernel launches per stage (cuFFT executions for FFT stages) */
+    int64_t stage_launches[WS_NSTAGES];/* kernel launches per stage */
 } ws_stats_t;
 
 typedef struct {
@@ -99,9 +100,9 @@ typedef struct {
 } ws_plan_info_t;
 
 /* Build a plan.
- *   N       image side, even, 16..32768
+ *   N       image side, a multiple of 8, 16..4096
  *   x0      image cropping parameter, 0 < x0 <= 0.5 (Section 3.3 box); N' is
- *           rounded up, so the effective x0 = N/(2 N') <= x0
+ *           rounded up, so the effective x0 = N/(2 N') <= x0; N' <= 6144
  *   W       least-misfit kernel width, 1..12
  *   fov     full field of view in direction cosines (l, m in [-fov/2, fov/2)),
  *           0 < fov and (fov/2)^2 * 2 < 1
@@ -140,7 +141,7 @@ ws_status ws_plan_info(ws_plan_t plan, ws_plan_info_t *info);
  * zero unless the plan was made with WS_FLAG_TIMING. */
 ws_status ws_plan_stats(ws_plan_t plan, ws_stats_t *stats, int32_t reset);
 
-/* Release the plan's device memory and cuFFT plans (waits for its work). */
+/* Release the plan's device memory (waits for its work). */
 ws_status ws_destroy(ws_plan_t plan);
 
 /* Message for the calling thread's latest non-WS_OK status ("" if none). */

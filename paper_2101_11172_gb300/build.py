@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libws_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["wstack.cu"]
+CU_SOURCES = ["wstack.cu", "transforms.cu"]
 CXX_SOURCES = ["plan.cpp", "lmfit.cpp"]
 
 
@@ -76,7 +76,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [o for _, o in jobs]
     libdir = os.path.join(home, "lib64")
     tmp = LIB + f".{os.getpid()}.tmp"
-    link = [nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs, "-L" + libdir, "-lcufft",
+    link = [nvcc, "-shared", *ARCH, "-cudart", "shared", "-o", tmp, *objs,
             "-Xlinker", "-rpath=" + libdir]
     subprocess.check_call(link)
     os.replace(tmp, LIB)

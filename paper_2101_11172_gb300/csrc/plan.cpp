@@ -5,7 +5,6 @@
 // ws_grid   Algorithm 5
 // ws_degrid Algorithm 6
 #include <cuda_runtime.h>
-#include <cufft.h>
 
 #include <algorithm>
 #include <cmath>
@@ -69,7 +68,6 @@ cudaError_t dev_alloc(T **ptr, size_t count, int64_t *bytes) {
 void release(ws_plan_s *p) {
     if (!p) return;
     DeviceScope scope(p->dev >= 0 ? p->dev : 0);
-    if (p->fft_made) cufftDestroy(p->fft);
     for (auto &t : p->pending) {
         cudaEventDestroy(t.start);
         cudaEventDestroy(t.stop);
@@ -79,6 +77,7 @@ void release(ws_plan_s *p) {
     cudaFree(p->d_corr);
     cudaFree(p->d_zsplit);
     cudaFree(p->d_stack);
+    cudaFree(p->d_tw);
     cudaFree(p->d_rec);
     cudaFree(p->d_list);
     cudaFree(p->d_counts);
@@ -146,7 +145,7 @@ struct StageTimer {
     cudaEvent_t a = nullptr, b = nullptr;
     StageTimer(ws_plan_s *p_, cudaStream_t s_, int stage_, int launches) : p(p_), s(s_), stage(stage_) {
         p->stats.stage_launches[stage] += launches;
-        if (stage != WS_STAGE_FFT_INV && stage != WS_STAGE_FFT_FWD) p->stats.kernel_launches += launches;
+        p->stats.kernel_launches += launches;
         if (!(p->flags & WS_FLAG_TIMING)) return;
         if (p->pending.size() > 4096) fold_pending(p);
         a = take_event(p);
@@ -163,6 +162,47 @@ struct StageTimer {
         }
     }
 };
+
+// Radices of an N'-point transform: 16, 8, 4 for the power of two (N' is a
+// multiple of 32, so no radix 2 is needed), then 7, 5, 3.
+bool fft_radices(int n, FftPlan *F) {
+    int a = 0, m = n;
+    while (m % 2 == 0) {
+        m /= 2;
+        ++a;
+    }
+    int ns = 0;
+    while (a > 0) {
+        int r;
+        if (a >= 8 || a == 4 || a == 7) r = 16;
+        else if (a == 3 || a == 5 || a == 6) r = 8;
+        else if (a == 2) r = 4;
+        else return false;
+        F->radix[ns++] = r;
+        a -= r == 16 ? 4 : (r == 8 ? 3 : 2);
+        if (ns >= 8) return false;
+    }
+    for (int p : {7, 5, 3})
+        while (m % p == 0) {
+            if (ns >= 8) return false;
+            F->radix[ns++] = p;
+            m /= p;
+        }
+    F->n = n;
+    F->nstages = ns;
+    return m == 1;
+}
+
+// Transforms per pass for `count` transforms on `nthr` threads within the
+// per-thread register budget of one FFT stage.
+bool fft_variant(FftPlan *F, int count, int nthr) {
+    for (int tpp = count; tpp >= 1; tpp /= 2)
+        if (fft_elements_needed(*F, tpp, nthr) <= fft_elements_budget()) {
+            F->tpp = tpp;
+            return true;
+        }
+    return false;
+}
 
 ws_status finish_call(ws_plan_s *p, cudaStream_t s) {
     cudaError_t e = cudaMemcpyAsync(p->h_drop, p->d_drop, 2 * sizeof(unsigned long long),
@@ -199,8 +239,8 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
         return WS_ERR_ARG;
     }
     *out = nullptr;
-    if (N < 16 || N > 32768 || N % 8) {
-        set_error("ws_plan: N must be a multiple of 8 in [16, 32768]");
+    if (N < 16 || N > 4096 || N % 8) {
+        set_error("ws_plan: N must be a multiple of 8 in [16, 4096]");
         return WS_ERR_ARG;
     }
     if (!(x0 > 0.0 && x0 <= 0.5)) {
@@ -225,8 +265,8 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
         return WS_ERR_ARG;
     }
     const int64_t Np = fft_size(N, x0);
-    if (Np > 65536) {
-        set_error("ws_plan: FFT grid larger than 65536");
+    if (Np > 6144) {
+        set_error("ws_plan: FFT grid N' = N/(2 x0) rounded up must not exceed 6144");
         return WS_ERR_ARG;
     }
     ws_plan_s *p = new (std::nothrow) ws_plan_s;
@@ -280,6 +320,19 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
     std::string err;
     if (!fit_least_misfit(W, p->x0, &p->fit, &err)) {
         set_error("ws_plan: " + err);
+        delete p;
+        return WS_ERR_ARG;
+    }
+    if (!fft_radices((int)Np, &p->fft2) || !fft_variant(&p->fft2, fft_per_cta(), fft_threads_pair())) {
+        set_error("ws_plan: no transform plan for N' = " + std::to_string(Np));
+        delete p;
+        return WS_ERR_ARG;
+    }
+    p->fft_mixed = (Np & (Np - 1)) != 0;
+    p->fft1 = p->fft2;
+    if (!fft_variant(&p->fft1, 1, fft_threads_one()) ||
+        transform_smem_bytes((int)Np, N) > (size_t)227 * 1024) {
+        set_error("ws_plan: no transform plan for N' = " + std::to_string(Np));
         delete p;
         return WS_ERR_ARG;
     }
@@ -350,6 +403,17 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
     WS_TRY(cudaMemcpy(p->d_zsplit, zs.data(), zs.size() * sizeof(float2), cudaMemcpyHostToDevice),
            "uploading z table");
     WS_TRY(dev_alloc(&p->d_stack, (size_t)P * Np * Np, &p->bytes), "allocating the w-stack chunk");
+    {
+        std::vector<float2> tw((size_t)Np);
+        for (int64_t m = 0; m < Np; ++m) {
+            const double ang = 2.0 * 3.14159265358979323846 * (double)m / (double)Np;
+            tw[m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+        }
+        WS_TRY(dev_alloc(&p->d_tw, tw.size(), &p->bytes), "allocating twiddles");
+        WS_TRY(cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice),
+               "uploading twiddles");
+    }
+    WS_TRY(setup_transform_kernels((int)Np, N), "configuring transform kernels");
     WS_TRY(dev_alloc(&p->d_counts, (size_t)p->ntiles + 1, &p->bytes), "allocating tile counts");
     WS_TRY(dev_alloc(&p->d_offsets, (size_t)p->ntiles + 1, &p->bytes), "allocating tile offsets");
     WS_TRY(dev_alloc(&p->d_blocksums, (size_t)4096, &p->bytes), "allocating scan sums");
@@ -359,43 +423,12 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
     WS_TRY(cudaMallocHost((void **)&p->h_drop, 2 * sizeof(unsigned long long)), "allocating pinned counters");
     std::memset(p->h_drop, 0, 2 * sizeof(unsigned long long));
 #undef WS_TRY
-    {
-        int n[2] = {(int)Np, (int)Np};
-        p->fft_batch = TT;
-        cufftResult r = cufftPlanMany(&p->fft, 2, n, nullptr, 1, (int)(Np * Np), nullptr, 1, (int)(Np * Np),
-                                      CUFFT_C2C, p->fft_batch);
-        if (r != CUFFT_SUCCESS) {
-            set_error("ws_plan: cufftPlanMany failed with code " + std::to_string((int)r));
-            release(p);
-            return r == CUFFT_ALLOC_FAILED ? WS_ERR_OOM : WS_ERR_CUDA;
-        }
-        p->fft_made = true;
-        size_t ws_bytes = 0;
-        if (cufftGetSize(p->fft, &ws_bytes) == CUFFT_SUCCESS) p->bytes += (int64_t)ws_bytes;
-    }
     *out = p;
     return WS_OK;
 fail:
     st = cuda_fail(e, what);
     release(p);
     return st;
-}
-
-static ws_status run_ffts(ws_plan_s *p, int planes, int direction, cudaStream_t s) {
-    if (cufftSetStream(p->fft, s) != CUFFT_SUCCESS) {
-        set_error("cufftSetStream failed");
-        return WS_ERR_CUDA;
-    }
-    const size_t plane = (size_t)p->L.Np * p->L.Np;
-    for (int q = 0; q < planes; q += p->fft_batch) {
-        cufftComplex *ptr = reinterpret_cast<cufftComplex *>(p->d_stack + q * plane);
-        cufftResult r = cufftExecC2C(p->fft, ptr, ptr, direction);
-        if (r != CUFFT_SUCCESS) {
-            set_error("cufftExecC2C failed with code " + std::to_string((int)r));
-            return WS_ERR_CUDA;
-        }
-    }
-    return WS_OK;
 }
 
 ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M, void *dirty,
@@ -435,14 +468,14 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
                 return cuda_fail(e, "ws_grid: grid3d kernel");
         }
         {
-            StageTimer t(p, s, WS_STAGE_FFT_INV, (planes + p->fft_batch - 1) / p->fft_batch);
-            if ((st = run_ffts(p, planes, CUFFT_INVERSE, s)) != WS_OK) return st;
+            StageTimer t(p, s, WS_STAGE_COLS_INV, 1);
+            if ((e = launch_inv_cols(p, planes, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: inv_cols kernel");
         }
         {
-            StageTimer t(p, s, WS_STAGE_SCREEN, 1);
-            if ((e = launch_screen_accum(p, c, planes, c == 0, c == nchunks - 1, static_cast<float2 *>(dirty),
-                                         s)) != cudaSuccess)
-                return cuda_fail(e, "ws_grid: screen kernel");
+            StageTimer t(p, s, WS_STAGE_ROWS_INV, 1);
+            if ((e = launch_inv_rows(p, c, planes, c == 0, c == nchunks - 1, static_cast<float2 *>(dirty), s)) !=
+                cudaSuccess)
+                return cuda_fail(e, "ws_grid: inv_rows kernel");
         }
     }
     return finish_call(p, s);
@@ -488,13 +521,13 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
     for (int c = 0; c < nchunks; ++c) {
         const int planes = std::min(p->P, total - c * p->P);
         {
-            StageTimer t(p, s, WS_STAGE_PRESCREEN, 1);
-            if ((e = launch_prescreen(p, c, planes, s)) != cudaSuccess)
-                return cuda_fail(e, "ws_degrid: prescreen kernel");
+            StageTimer t(p, s, WS_STAGE_ROWS_FWD, 1);
+            if ((e = launch_fwd_rows(p, c, planes, s)) != cudaSuccess)
+                return cuda_fail(e, "ws_degrid: fwd_rows kernel");
         }
         {
-            StageTimer t(p, s, WS_STAGE_FFT_FWD, (planes + p->fft_batch - 1) / p->fft_batch);
-            if ((st = run_ffts(p, planes, CUFFT_FORWARD, s)) != WS_OK) return st;
+            StageTimer t(p, s, WS_STAGE_COLS_FWD, 1);
+            if ((e = launch_fwd_cols(p, planes, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: fwd_cols kernel");
         }
         {
             StageTimer t(p, s, WS_STAGE_DEGRID3D, 1);

@@ -1,0 +1,233 @@
+// Fused plane transforms of the improved W-stacking method (sm_103a).
+//
+// Degridding (Algorithm 6 steps 3a-3c) for plane t:
+//   Q_t = pad_{N'}( g exp(-2 pi i t z) ),  g = h_x h_y h_z f   (image, N x N)
+//   F_t[S][R] = sum_{I,J} Q_t[I][J] exp(-2 pi i (S I + R J) / N')
+// is split into
+//   fwd_rows  (screen + zero pad + DFT over J, only the N image rows I)
+//   fwd_cols  (zero pad in I + DFT over I, every column R, all N' outputs S).
+// Gridding (Algorithm 5 steps 3b-5) for plane t:
+//   P_t[I][J] = sum_{S,R} G_t[S][R] exp(+2 pi i (S I + R J) / N'), kept on the crop
+//   D[I][J]  += P_t[I][J] exp(+2 pi i t z[I][J])   (sum over t, compensated)
+//   dirty     = h_x h_y h_z D
+// is split into
+//   inv_cols  (DFT over S of every column R, only the N crop rows I kept)
+//   inv_rows  (DFT over R of each crop row, crop columns J, screen, sum over t).
+// Zero padding is never stored or read (the first FFT stage produces zeros
+// itself) and the crop is applied by the last stage's stores.  The
+// intermediate (N crop rows x N' columns) stays in place in rows 0..N-1 of
+// each column block of the plane (layout in common.cuh).
+#include "common.cuh"
+#include "fft.cuh"
+#include "ws_internal.hpp"
+
+namespace ws {
+namespace {
+
+constexpr int kThreads = 512;       // two rows or two columns per CTA
+constexpr int kPerCta = 2;
+constexpr int kRowThreads = 256;    // one row per CTA (inv_rows)
+constexpr int kEPT = 16;            // elements a thread holds in one FFT stage
+
+__device__ __forceinline__ int grid_to_crop(int g, int half, int Np) { return g < half ? g + half : g - (Np - half); }
+__device__ __forceinline__ bool in_crop(int g, int half, int Np) { return g < half || g >= Np - half; }
+
+// -- degridding --------------------------------------------------------------
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads, 1)
+fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ img,
+                const float2 *__restrict__ zsplit, int plane0, float2 *__restrict__ stack) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, N = L.N, half = N / 2;
+    const int ii0 = blockIdx.x * kPerCta;
+    const float t = (float)(plane0 + (int)blockIdx.y + L.t_lo);   // blockIdx is unsigned: convert before adding t_lo
+    float2 *plane = stack + (size_t)blockIdx.y * Np * Np;
+    auto load = [&](int b, int J) -> float2 {
+        if (!in_crop(J, half, Np)) return make_float2(0.f, 0.f);
+        const size_t pix = (size_t)(ii0 + b) * N + grid_to_crop(J, half, Np);
+        const float2 g = __ldg(img + pix);
+        float sn, cs;
+        phase_tz(t, __ldg(zsplit + pix), &sn, &cs);          // times exp(-i phi)
+        return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+    };
+    auto store = [&](int b, int R, float2 v) { __stcs(plane + tiled_index(ii0 + b, R, Np), v); };
+    fft_many<kEPT, MIXED>(sbuf, fft_padded_len(Np), kPerCta, F, tw, false, threadIdx.x, kThreads, load, store);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads, 1)
+fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, float2 *__restrict__ stack) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, half = L.N / 2;
+    const int R0 = blockIdx.x * kPerCta;                  // two of the four columns of a block
+    float2 *blk = stack + (size_t)blockIdx.y * Np * Np + (size_t)(R0 >> 2) * Np * CB + (R0 & 3);
+    // rows 0..N-1 hold the N transformed image rows; every other row is zero padding
+    auto load = [&](int b, int S) -> float2 {
+        if (!in_crop(S, half, Np)) return make_float2(0.f, 0.f);
+        return __ldcs(blk + (size_t)grid_to_crop(S, half, Np) * CB + b);
+    };
+    auto store = [&](int b, int S, float2 v) { blk[(size_t)S * CB + b] = v; };
+    fft_many<kEPT, MIXED>(sbuf, fft_padded_len(Np), kPerCta, F, tw, false, threadIdx.x, kThreads, load, store);
+}
+
+// -- gridding ----------------------------------------------------------------
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kThreads, 1)
+inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, float2 *__restrict__ stack) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, half = L.N / 2;
+    const int R0 = blockIdx.x * kPerCta;
+    float2 *blk = stack + (size_t)blockIdx.y * Np * Np + (size_t)(R0 >> 2) * Np * CB + (R0 & 3);
+    auto load = [&](int b, int S) -> float2 { return __ldcs(blk + (size_t)S * CB + b); };
+    // keep the N crop rows, compacted into rows 0..N-1 (all reads precede these writes)
+    auto store = [&](int b, int S, float2 v) {
+        if (in_crop(S, half, Np)) blk[(size_t)grid_to_crop(S, half, Np) * CB + b] = v;
+    };
+    fft_many<kEPT, MIXED>(sbuf, fft_padded_len(Np), kPerCta, F, tw, true, threadIdx.x, kThreads, load, store);
+}
+
+// float2 slots of one padded row, rounded up to an even count so that the
+// float4 array placed after it (and after the even-length z row) is 16-byte aligned
+__host__ __device__ constexpr int row_slots(int Np) { return (fft_padded_len(Np) + 1) & ~1; }
+
+// One CTA owns image row ii and sums the chunk's planes into a compensated
+// accumulator in shared memory; the last FFT stage screens and accumulates.
+template <bool MIXED>
+__global__ void __launch_bounds__(kRowThreads, 2)
+inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ stack,
+                int plane0, int planes, const float2 *__restrict__ zsplit, const float *__restrict__ corr,
+                float4 *__restrict__ acc, int first, int last, float2 *__restrict__ dirty) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, N = L.N, half = N / 2;
+    float2 *zrow = sbuf + row_slots(Np);                         // N
+    float4 *srow = reinterpret_cast<float4 *>(zrow + N);         // N: (sum re, sum im, comp re, comp im)
+    const int ii = blockIdx.x;
+    const int tid = threadIdx.x;
+    const size_t pix0 = (size_t)ii * N;
+    for (int jj = tid; jj < N; jj += kRowThreads) {
+        zrow[jj] = zsplit[pix0 + jj];
+        srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
+    }
+    __syncthreads();
+    const int nvalid = min(planes, L.Nw - plane0);
+    for (int p = 0; p < nvalid; ++p) {
+        const float2 *plane = stack + (size_t)p * Np * Np;
+        const float t = (float)(plane0 + p + L.t_lo);
+        auto load = [&](int, int R) -> float2 { return __ldcs(plane + tiled_index(ii, R, Np)); };
+        auto store = [&](int, int J, float2 v) {
+            if (!in_crop(J, half, Np)) return;
+            const int jj = grid_to_crop(J, half, Np);
+            float sn, cs;
+            phase_tz(t, zrow[jj], &sn, &cs);
+            float4 a = srow[jj];
+            kahan_add(a.x, a.z, v.x * cs - v.y * sn);
+            kahan_add(a.y, a.w, v.x * sn + v.y * cs);
+            srow[jj] = a;
+        };
+        fft_many<kEPT, MIXED>(sbuf, 0, 1, F, tw, true, tid, kRowThreads, load, store);
+        __syncthreads();
+    }
+    for (int jj = tid; jj < N; jj += kRowThreads) {
+        const float4 a = srow[jj];
+        if (last) {
+            const float h = corr[pix0 + jj];
+            dirty[pix0 + jj] = make_float2(h * (a.x - a.z), h * (a.y - a.w));
+        } else {
+            acc[pix0 + jj] = a;
+        }
+    }
+}
+
+size_t smem2(int Np) { return (size_t)kPerCta * fft_padded_len(Np) * sizeof(float2); }
+size_t smem_rows(int Np, int N) {
+    return (size_t)row_slots(Np) * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4));
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+// Largest thread-elements need of one stage when `tpp` transforms run together.
+int fft_elements_needed(const FftPlan &F, int tpp, int nthr) {
+    int need = 0;
+    for (int s = 0; s < F.nstages; ++s) {
+        const int R = F.radix[s];
+        const int per = (tpp * (F.n / R) + nthr - 1) / nthr;
+        need = need > per * R ? need : per * R;
+    }
+    return need;
+}
+
+int fft_elements_budget() { return kEPT; }
+int fft_threads_pair() { return kThreads; }
+int fft_threads_one() { return kRowThreads; }
+int fft_per_cta() { return kPerCta; }
+
+size_t transform_smem_bytes(int Np, int N) { return smem2(Np) > smem_rows(Np, N) ? smem2(Np) : smem_rows(Np, N); }
+
+cudaError_t setup_transform_kernels(int Np, int N) {
+    cudaError_t e;
+    const size_t s2 = smem2(Np), s1 = smem_rows(Np, N);
+    if ((e = allow_smem(fwd_rows_kernel<false>, s2)) != cudaSuccess) return e;
+    if ((e = allow_smem(fwd_rows_kernel<true>, s2)) != cudaSuccess) return e;
+    if ((e = allow_smem(fwd_cols_kernel<false>, s2)) != cudaSuccess) return e;
+    if ((e = allow_smem(fwd_cols_kernel<true>, s2)) != cudaSuccess) return e;
+    if ((e = allow_smem(inv_cols_kernel<false>, s2)) != cudaSuccess) return e;
+    if ((e = allow_smem(inv_cols_kernel<true>, s2)) != cudaSuccess) return e;
+    if ((e = allow_smem(inv_rows_kernel<false>, s1)) != cudaSuccess) return e;
+    if ((e = allow_smem(inv_rows_kernel<true>, s1)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
+    const dim3 grid(p->L.N / kPerCta, planes);
+    const size_t smem = smem2(p->L.Np);
+    if (p->fft_mixed)
+        fwd_rows_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_img, p->d_zsplit,
+                                                           chunk * p->P, p->d_stack);
+    else
+        fwd_rows_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_img, p->d_zsplit,
+                                                            chunk * p->P, p->d_stack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_cols(const ws_plan_s *p, int planes, cudaStream_t s) {
+    const dim3 grid(p->L.Np / kPerCta, planes);
+    const size_t smem = smem2(p->L.Np);
+    if (p->fft_mixed)
+        fwd_cols_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+    else
+        fwd_cols_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_cols(const ws_plan_s *p, int planes, cudaStream_t s) {
+    const dim3 grid(p->L.Np / kPerCta, planes);
+    const size_t smem = smem2(p->L.Np);
+    if (p->fft_mixed)
+        inv_cols_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+    else
+        inv_cols_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
+                            cudaStream_t s) {
+    const size_t smem = smem_rows(p->L.Np, p->L.N);
+    if (p->fft_mixed)
+        inv_rows_kernel<true><<<p->L.N, kRowThreads, smem, s>>>(p->L, p->fft1, p->d_tw, p->d_stack, chunk * p->P,
+                                                                planes, p->d_zsplit, p->d_corr, p->d_acc, first,
+                                                                last, dirty);
+    else
+        inv_rows_kernel<false><<<p->L.N, kRowThreads, smem, s>>>(p->L, p->fft1, p->d_tw, p->d_stack, chunk * p->P,
+                                                                 planes, p->d_zsplit, p->d_corr, p->d_acc, first,
+                                                                 last, dirty);
+    return cudaGetLastError();
+}
+
+}  // namespace ws

@@ -2,13 +2,13 @@
 #pragma once
 
 #include <cuda_runtime.h>
-#include <cufft.h>
 #include <stdint.h>
 
 #include <string>
 #include <vector>
 
 #include "../../include/ws.h"
+#include "fft_plan.hpp"
 #include "lmfit.hpp"
 
 namespace ws {
@@ -16,8 +16,8 @@ namespace ws {
 // Gridding tile owned by one CTA of the gridding kernel: TT w-planes x TV
 // grid rows (v) x TU grid columns (u).  N' is a multiple of 32, so TU and TV
 // divide it; the plane count is padded to a multiple of TT.
-constexpr int TU = 32;
-constexpr int TV = 16;
+constexpr int TU = 16;
+constexpr int TV = 32;
 constexpr int TT = 8;
 constexpr int kMaxW = 12;
 constexpr int kMaxDeg = 16;
@@ -62,10 +62,10 @@ struct ws_plan_s {
     float2 *d_zsplit = nullptr;    // N x N: z = hi + lo, hi a multiple of 2^-13
     // stack workspace
     int P = 0;                     // planes per chunk (multiple of TT)
-    float2 *d_stack = nullptr;     // P x N' x N'
-    int fft_batch = 0;
-    cufftHandle fft = 0;           // batch fft_batch
-    bool fft_made = false;
+    float2 *d_stack = nullptr;     // P x N' x N', column-block layout (common.cuh)
+    float2 *d_tw = nullptr;        // N' twiddles exp(-2 pi i m / N')
+    ws::FftPlan fft2{}, fft1{};    // two rows / columns per CTA, one row per CTA
+    bool fft_mixed = false;        // N' has a factor 3, 5 or 7
     // per-call buffers (grow on demand)
     ws::VisRec *d_rec = nullptr;
     int64_t rec_cap = 0;
@@ -101,11 +101,22 @@ cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis
                         bool grid, cudaStream_t s);
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
 cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
-cudaError_t launch_screen_accum(const ws_plan_s *p, int chunk, int planes, bool first, bool last,
-                                float2 *dirty, cudaStream_t s);
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s);
-cudaError_t launch_prescreen(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64_t M,
                                 float2 *vis, cudaStream_t s);
+
+// Plane transforms (transforms.cu).
+int fft_elements_needed(const FftPlan &F, int tpp, int nthr);
+int fft_elements_budget();
+int fft_threads_pair();
+int fft_threads_one();
+int fft_per_cta();
+size_t transform_smem_bytes(int Np, int N);
+cudaError_t setup_transform_kernels(int Np, int N);
+cudaError_t launch_fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
+cudaError_t launch_fwd_cols(const ws_plan_s *p, int planes, cudaStream_t s);
+cudaError_t launch_inv_cols(const ws_plan_s *p, int planes, cudaStream_t s);
+cudaError_t launch_inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
+                            cudaStream_t s);
 
 }  // namespace ws

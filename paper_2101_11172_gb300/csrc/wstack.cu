@@ -1,28 +1,26 @@
 // CUDA kernels of the improved W-stacking hot path (sm_103a).
 //
-// Gridding (Algorithm 5):   prep -> bin -> per plane chunk: grid3d -> inverse FFT (cuFFT)
-//                           -> screen_accum (crop, x exp(2 pi i t z), sum over t, x h_x h_y h_z)
+// Gridding (Algorithm 5):   prep -> bin -> per plane chunk: grid3d -> inv_cols -> inv_rows
+//                           (transforms.cu: inverse DFTs, crop, x exp(2 pi i t z), sum over t,
+//                           x h_x h_y h_z)
 // Degridding (Algorithm 6): prep -> bin -> correct_image (x h_x h_y h_z) -> per plane chunk:
-//                           prescreen (x exp(-2 pi i t z), zero pad) -> forward FFT (cuFFT)
-//                           -> degrid3d (3-D correlation with C_x C_y C_z, x exp(-2 pi i w (n0-1)))
+//                           fwd_rows -> fwd_cols (transforms.cu: x exp(-2 pi i t z), zero pad,
+//                           forward DFTs) -> degrid3d (3-D correlation with C_x C_y C_z,
+//                           x exp(-2 pi i w (n0-1)))
 //
-// Grid layout: plane p of a chunk holds N' x N' complex64 values, row s
-// (v direction) major, column r (u direction) minor, both stored modulo N'.
-// Because exp(2 pi i r j / N') is N'-periodic in r, a tap that runs past the
-// grid edge wraps onto the opposite edge and the inverse DFT of the wrapped
-// grid is exactly the sum over all integers r of Eq. gridded-dirty-map; the
-// centred crop |x| < x0 is then rows/columns [N'-N/2, N') and [0, N/2).
+// Grid indices: row s (v direction) and column r (u direction) of a plane are
+// stored modulo N'.  Because exp(2 pi i r j / N') is N'-periodic in r, a tap
+// that runs past the grid edge wraps onto the opposite edge and the inverse
+// DFT of the wrapped grid is exactly the sum over all integers r of Eq.
+// gridded-dirty-map; the centred crop |x| < x0 is then rows/columns
+// [N'-N/2, N') and [0, N/2).  Planes use the column-block layout of common.cuh.
 #include <math.h>
 
+#include "common.cuh"
 #include "ws_internal.hpp"
 
 namespace ws {
 namespace {
-
-__device__ __forceinline__ int wrap_add(int a, int b, int n) {
-    int s = a + b;
-    return s >= n ? s - n : s;
-}
 
 // c_i(nu) by Horner's rule on the monomial table (FP32).
 __device__ __forceinline__ float tap_weight(const float *__restrict__ coef, int deg, int i, float nu) {
@@ -42,22 +40,6 @@ __device__ __forceinline__ void warp_weights(const float *__restrict__ coef, int
         swt[lane] = tap_weight(coef, deg, i, nu);
     }
     __syncwarp();
-}
-
-// exp(2 pi i t z) with z = hi + lo split so that t * hi is exact in FP32
-// (hi is a multiple of 2^-13 of magnitude <= 1/2 and |t| < 2^11): the phase in
-// turns is frac(t hi) + t lo, reduced exactly before the single rounding.
-__device__ __forceinline__ void phase_tz(float t, float2 z, float *s, float *c) {
-    float hi = t * z.x;
-    float turns = fmaf(t, z.y, hi - rintf(hi));
-    sincospif(2.0f * turns, s, c);
-}
-
-__device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
-    float y = v - comp;
-    float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
 }
 
 // ---------------------------------------------------------------------------
@@ -286,62 +268,15 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     __syncthreads();
     const size_t plane = (size_t)Np * Np;
     const int p0 = t_org - chunk_tt0 * TT;
+    // pairs of cells, ordered (plane, column block, row, pair) so that each
+    // column block's TV rows go out as one contiguous run
     for (int i = threadIdx.x; i < kTileCells / 2; i += kGridThreads) {
-        const int cell = 2 * i;
-        const int lc = cell % TU, lr = (cell / TU) % TV, pl = cell / (TU * TV);
+        const int pair = i & 1, lr = (i >> 1) % TV, blk = (i / (2 * TV)) % (TU / CB), pl = i / (TU * TV / 2);
+        const int lc = blk * CB + 2 * pair;
+        const int cell = (pl * TV + lr) * TU + lc;
         float4 v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
-        float2 *dst = stack + (size_t)(p0 + pl) * plane + (size_t)(v_org + lr) * Np + u_org + lc;
+        float2 *dst = stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np);
         *reinterpret_cast<float4 *>(dst) = v;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Algorithm 5 steps 3c-5: crop, x exp(2 pi i t z(x, y)), sum over t (Kahan),
-// and on the last chunk x h_x(x) h_y(y) h_z(z(x, y)).  One thread per pair
-// of adjacent pixels, looping over the chunk's planes.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-screen_accum_kernel(Launch L, const float2 *__restrict__ stack, int plane0, int planes,
-                    const float2 *__restrict__ zsplit, const float *__restrict__ corr,
-                    float4 *__restrict__ acc, int first, int last, float2 *__restrict__ dirty) {
-    const int N = L.N, Np = L.Np, half = N / 2;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)N * half) return;
-    const int ii = (int)(q / half), jj = (int)(q % half) * 2;
-    const int prow = ii < half ? ii - half + Np : ii - half;
-    const int pcol = jj < half ? jj - half + Np : jj - half;
-    const int64_t pix = (int64_t)ii * N + jj;
-    const float2 z0 = zsplit[pix], z1 = zsplit[pix + 1];
-    float4 s0, s1;                 // (sum re, sum im, comp re, comp im) of the two pixels
-    if (first) {
-        s0 = make_float4(0.f, 0.f, 0.f, 0.f);
-        s1 = s0;
-    } else {
-        s0 = acc[pix];
-        s1 = acc[pix + 1];
-    }
-    const size_t plane = (size_t)Np * Np;
-    const float4 *src = reinterpret_cast<const float4 *>(stack + (size_t)prow * Np + pcol);
-    const int nvalid = min(planes, L.Nw - plane0);
-#pragma unroll 4
-    for (int p = 0; p < nvalid; ++p) {
-        const float4 v = __ldcs(src + p * (plane / 2));
-        const float t = (float)(plane0 + p + L.t_lo);
-        float sn, cs;
-        phase_tz(t, z0, &sn, &cs);
-        kahan_add(s0.x, s0.z, v.x * cs - v.y * sn);
-        kahan_add(s0.y, s0.w, v.x * sn + v.y * cs);
-        phase_tz(t, z1, &sn, &cs);
-        kahan_add(s1.x, s1.z, v.z * cs - v.w * sn);
-        kahan_add(s1.y, s1.w, v.z * sn + v.w * cs);
-    }
-    if (last) {
-        const float h0 = corr[pix], h1 = corr[pix + 1];
-        *reinterpret_cast<float4 *>(dirty + pix) =
-            make_float4(h0 * (s0.x - s0.z), h0 * (s0.y - s0.w), h1 * (s1.x - s1.z), h1 * (s1.y - s1.w));
-    } else {
-        acc[pix] = s0;
-        acc[pix + 1] = s1;
     }
 }
 
@@ -355,50 +290,12 @@ __global__ void correct_image_kernel(int64_t n, const float *__restrict__ corr,
     out[i] = make_float2(h * f.x, h * f.y);
 }
 
-// Algorithm 6 steps 3a-3b: x exp(-2 pi i t z(x, y)) and zero padding to
-// N' x N', for every plane of the chunk.  One thread per two adjacent grid
-// cells of a row, looping over planes.
-__global__ void __launch_bounds__(256)
-prescreen_kernel(Launch L, const float2 *__restrict__ img, const float2 *__restrict__ zsplit,
-                 int plane0, int planes, float2 *__restrict__ stack) {
-    const int N = L.N, Np = L.Np, half = N / 2;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)Np * (Np / 2)) return;
-    const int R = (int)(q / (Np / 2)), C = (int)(q % (Np / 2)) * 2;
-    const size_t plane = (size_t)Np * Np;
-    float4 *dst = reinterpret_cast<float4 *>(stack + (size_t)R * Np + C);
-    const bool rin = R < half || R >= Np - half;
-    const bool cin = C < half || C >= Np - half;     // C even and N/2 even: both cells agree
-    if (!(rin && cin)) {
-        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int p = 0; p < planes; ++p) __stcs(dst + p * (plane / 2), zero);
-        return;
-    }
-    const int ii = R < half ? R + half : R - (Np - half);
-    const int jj = C < half ? C + half : C - (Np - half);
-    const int64_t pix = (int64_t)ii * N + jj;
-    const float2 g0 = img[pix], g1 = img[pix + 1];
-    const float2 z0 = zsplit[pix], z1 = zsplit[pix + 1];
-#pragma unroll 4
-    for (int p = 0; p < planes; ++p) {
-        const float t = (float)(plane0 + p + L.t_lo);
-        float sn, cs;
-        float4 o;
-        phase_tz(t, z0, &sn, &cs);            // multiply by exp(-i phi) = cs - i sn
-        o.x = g0.x * cs + g0.y * sn;
-        o.y = g0.y * cs - g0.x * sn;
-        phase_tz(t, z1, &sn, &cs);
-        o.z = g1.x * cs + g1.y * sn;
-        o.w = g1.y * cs - g1.x * sn;
-        __stcs(dst + p * (plane / 2), o);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Degridding: Algorithm 6 steps 4-5.  One warp per visibility (visiting them
-// in tile order for cache reuse); lane <-> (row b, plane c) pair of the
-// footprint, W contiguous columns per lane, then a warp reduction.  Each
-// chunk adds its planes' share to vis in chunk order.
+// in tile order for cache reuse).  Lane <-> (column a, row b) pair of the
+// W x W footprint; each lane walks the footprint's planes, so at every plane
+// the warp reads W contiguous rows of 2-3 column blocks.  Each chunk adds its
+// planes' share to vis, in chunk order.
 // ---------------------------------------------------------------------------
 constexpr int kDegridThreads = 256;
 
@@ -422,21 +319,18 @@ degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec 
     float ar = 0.f, ai = 0.f;
     const size_t plane = (size_t)Np * Np;
     for (int pair = lane; pair < W * W; pair += 32) {
-        const int b = pair % W, c = pair / W;
-        if (c < c_lo || c > c_hi) continue;
-        const float2 *row = stack + (size_t)(r.t0 + c - plane0) * plane + (size_t)wrap_add(r.s0, b, Np) * Np;
+        const int a = pair % W, b = pair / W;
+        const float2 *cell = stack + tiled_index(wrap_add(r.s0, b, Np), wrap_add(r.r0, a, Np), Np);
         float sr = 0.f, si = 0.f;
-        int col = r.r0;
-        for (int a = 0; a < W; ++a) {
-            const float2 f = __ldg(row + col);
-            const float wa = wt[a];
-            sr = fmaf(wa, f.x, sr);
-            si = fmaf(wa, f.y, si);
-            col = col + 1 == Np ? 0 : col + 1;
+        for (int c = c_lo; c <= c_hi; ++c) {
+            const float2 f = __ldg(cell + (size_t)(r.t0 + c - plane0) * plane);
+            const float wc = wt[2 * W + c];
+            sr = fmaf(wc, f.x, sr);
+            si = fmaf(wc, f.y, si);
         }
-        const float wbc = wt[W + b] * wt[2 * W + c];
-        ar = fmaf(wbc, sr, ar);
-        ai = fmaf(wbc, si, ai);
+        const float wab = wt[a] * wt[W + b];
+        ar = fmaf(wab, sr, ar);
+        ai = fmaf(wab, si, ai);
     }
     for (int o = 16; o > 0; o >>= 1) {
         ar += __shfl_xor_sync(0xffffffffu, ar, o);
@@ -498,25 +392,9 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_screen_accum(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
-                                cudaStream_t s) {
-    const int64_t n = (int64_t)p->L.N * (p->L.N / 2);
-    screen_accum_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p->L, p->d_stack, chunk * p->P, planes, p->d_zsplit,
-                                                          p->d_corr, p->d_acc, first ? 1 : 0, last ? 1 : 0,
-                                                          dirty);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s) {
     const int64_t n = (int64_t)p->L.N * p->L.N;
     correct_image_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, p->d_corr, image, p->d_img);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_prescreen(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
-    const int64_t n = (int64_t)p->L.Np * (p->L.Np / 2);
-    prescreen_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p->L, p->d_img, p->d_zsplit, chunk * p->P, planes,
-                                                       p->d_stack);
     return cudaGetLastError();
 }
 

@@ -150,3 +150,13 @@ def survey(N: int = 2048, n_ant: int = 256, n_times: int = 306, fov: float = 0.5
     M = uvw.shape[0]
     vis = complex_normal(M, rng_for(index, 3)) + complex_normal(M, rng_for(index, 4), sigma)
     return Workload(f"survey-N{N}-M{M}", N, x0, W, fov, uvw, image, vis)
+
+
+def survey_slab(w_half: float = 35.0, **kw) -> Workload:
+    """The survey workload restricted to |w| < w_half: same image, grid and
+    array, about 1.8 million visibilities on 17 w-planes (a small
+    case for profiling the per-plane kernels)."""
+    wl = survey(**kw)
+    sel = abs(wl.uvw[:, 2]) < w_half
+    return Workload(f"survey-slab-N{wl.N}-w{w_half:g}", wl.N, wl.x0, wl.W, wl.fov, wl.uvw[sel], wl.image,
+                    wl.vis[sel])
