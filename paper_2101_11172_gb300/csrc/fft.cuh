@@ -1,21 +1,21 @@
 // FFT engine for the w-plane transforms (Algorithm 5 step 3b, Algorithm 6
 // step 3c).
 //
-// A CTA transforms a few length-n sequences cooperatively with the Stockham
-// autosort formulation (every stage reads its butterfly inputs at stride n/R
-// and writes them grouped by the running transform size Ns, so no
-// bit-reversal pass is needed).  The first stage takes its inputs straight
-// from the caller (global memory, with zero padding and screens applied on
-// the fly) into registers and the last stage hands its outputs straight back
-// (global stores, crops, accumulations); only the stages in between go
-// through shared memory, in place: a stage loads all of its butterflies into
-// registers and only then, after a barrier, stores the results.  Radices: 16,
-// 8, 4 (power-of-two part) and 7, 5, 3.  Twiddles come from a table of
+// A CTA transforms one or two length-n sequences cooperatively with mixed-
+// radix decimation in time, in place in shared memory.  The first stage reads
+// its inputs straight from the caller (global memory, with zero padding and
+// screens applied on the fly), transforms them in registers and scatters them
+// to digit-reversed positions; every later stage reads, twiddles, transforms
+// and writes back the same R positions, so a thread holds one butterfly at a
+// time and a stage needs a single barrier; the last stage hands its outputs
+// straight back (global stores, crops, accumulations).  Radices: 16, 8, 4
+// (power-of-two part) and 7, 5, 3.  Twiddles come from a table of
 // exp(-2 pi i m / n) computed in double precision on the host.
 //
-// Shared-memory addressing pads one element every 16 (pad(e) = e + e/16),
-// which keeps the strided accesses of the radix-16/8 stages free of bank
-// conflicts.
+// Shared-memory addressing inserts one pad slot after every n / radix[0]
+// elements (a power of two), which removes the bank conflicts of the
+// digit-reversed scatter for the main sizes; two transforms of a CTA sit
+// 8 (mod 16) slots apart so interleaved lanes use different banks.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -149,110 +149,130 @@ __device__ __forceinline__ void dft<7>(float2 *v, bool inv, const float2 *__rest
     dft_odd<7>(v, inv, tw, n);
 }
 
-// One Stockham stage of radix R over `count` transforms.  Work item q maps to
-// transform t = q % count and butterfly j = q / count (transforms interleaved
-// so neighbouring lanes touch neighbouring columns of global memory).  The
-// first stage reads its inputs through load(t, e) and the last stage hands
-// its outputs to store(t, e, v); the others use the padded shared buffers
-// (buf + t * stride).  EPT bounds the elements one thread holds (the host
-// checks ceil(count * n / R / nthr) * R <= EPT).
-template <int R, int EPT, class Load, class Store>
-__device__ __forceinline__ void stage(float2 *buf, int stride, int count, int n, int Ns, bool first, bool last,
-                                      const float2 *__restrict__ tw, bool inv, int tid, int nthr, Load &load,
-                                      Store &store) {
-    constexpr int MAXB = EPT / R;
-    const int nb = n / R;
-    const int total = count * nb;
-    const int twstep = n / (Ns * R);
-    float2 v[MAXB > 0 ? MAXB : 1][R];
+// In-place decimation-in-time stage of radix R: for every block b of R*L
+// positions and offset k < L, the R elements at b*R*L + k + m*L (m < R) are
+// multiplied by w_{RL}^{k m}, transformed by an R-point DFT and written back
+// to the same positions.  Butterflies own disjoint positions, so a thread
+// can do them one after another and a stage needs no barrier between its
+// reads and writes.  Work item q -> transform t = q % COUNT, butterfly q / COUNT.
+// POW2: n, R and L are powers of two and the index arithmetic uses shifts.
+template <int R, int COUNT, bool POW2, class Store>
+__device__ __forceinline__ void dit_stage(float2 *buf, const FftPlan &P, int L, bool last,
+                                          const float2 *__restrict__ tw, bool inv, int tid, int nthr,
+                                          Store &store) {
+    const int n = P.n, nb = n / R, total = COUNT * nb;
+    int logL = 0, lgtw = 0;
+    if constexpr (POW2) {
+        logL = __ffs(L) - 1;
+        lgtw = P.logn - logL - (__ffs(R) - 1);
+    }
+    const int twstep = POW2 ? 0 : n / (R * L);
+    for (int q = tid; q < total; q += nthr) {
+        const int t = q % COUNT, bq = q / COUNT;
+        int blk, k;
+        if constexpr (POW2) {
+            blk = bq >> logL;
+            k = bq & (L - 1);
+        } else {
+            blk = bq / L;
+            k = bq - blk * L;
+        }
+        const int base = blk * R * L + k;
+        float2 *x = buf + t * P.stride;
+        float2 v[R];
 #pragma unroll
-    for (int b = 0; b < MAXB; ++b) {
-        const int q = tid + b * nthr;
-        if (q < total) {
-            const int t = q % count, j = q / count;
-            if (first) {
+        for (int m = 0; m < R; ++m) v[m] = x[fft_pad(base + m * L, P.padshift)];
+        if (k > 0) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[b][r] = load(t, j + r * nb);
-            } else {
-                const float2 *x = buf + t * stride;
+            for (int m = 1; m < R; ++m)
+                v[m] = cmul(v[m], twiddle(tw, POW2 ? (k * m) << lgtw : k * m * twstep, inv));
+        }
+        dft<R>(v, inv, tw, n);
+        if (last) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[b][r] = x[fft_pad(j + r * nb)];
-            }
-            if (Ns > 1) {
-                const int k = j % Ns;
+            for (int m = 0; m < R; ++m) store(t, base + m * L, v[m]);
+        } else {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twiddle(tw, (k * r * twstep) % n, inv));
-            }
-            dft<R>(v[b], inv, tw, n);
+            for (int m = 0; m < R; ++m) x[fft_pad(base + m * L, P.padshift)] = v[m];
         }
     }
-    if (last) {
+    if (!last) __syncthreads();
+}
+
+// First stage: butterfly j of each transform reads inputs m*(n/R) + j, m < R,
+// straight from load(t, e), and writes them to the digit-reversed positions
+// g*R + m that the later in-place stages expect (g = the digits of j in
+// reverse order).  A one-stage transform stores directly.
+template <int R, int COUNT, bool POW2, class Load, class Store>
+__device__ __forceinline__ void dit_first(float2 *buf, const FftPlan &P, const float2 *__restrict__ tw,
+                                          bool inv, int tid, int nthr, Load &load, Store &store) {
+    const int n = P.n, nb = n / R, total = COUNT * nb;
+    for (int q = tid; q < total; q += nthr) {
+        const int t = q % COUNT, j = q / COUNT;
+        float2 v[R];
 #pragma unroll
-        for (int b = 0; b < MAXB; ++b) {
-            const int q = tid + b * nthr;
-            if (q < total) {
-                const int t = q % count, j = q / count;
-                const int idx = (j / Ns) * Ns * R + (j % Ns);
+        for (int m = 0; m < R; ++m) v[m] = load(t, m * nb + j);
+        dft<R>(v, inv, tw, n);
+        if (P.nstages == 1) {
 #pragma unroll
-                for (int r = 0; r < R; ++r) store(t, idx + r * Ns, v[b][r]);
-            }
+            for (int m = 0; m < R; ++m) store(t, m, v[m]);
+            continue;
         }
-        return;
-    }
-    if (!first) __syncthreads();          // every read of this stage done before any write
-#pragma unroll
-    for (int b = 0; b < MAXB; ++b) {
-        const int q = tid + b * nthr;
-        if (q < total) {
-            const int t = q % count, j = q / count;
-            float2 *x = buf + t * stride;
-            const int idx = (j / Ns) * Ns * R + (j % Ns);
-#pragma unroll
-            for (int r = 0; r < R; ++r) x[fft_pad(idx + r * Ns)] = v[b][r];
+        int g = 0;
+        for (int i = 1; i < P.nstages; ++i) {
+            if constexpr (POW2)
+                g += ((j >> P.lxw[i]) & (P.radix[i] - 1)) << P.lgw[i];
+            else
+                g += ((j / P.xw[i]) % P.radix[i]) * P.gw[i];
         }
+        float2 *x = buf + t * P.stride;
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[fft_pad(g * R + m, P.padshift)] = v[m];
     }
-    __syncthreads();
+    if (P.nstages > 1) __syncthreads();
 }
 
 }  // namespace fftdev
 
-// Transform `count` sequences of length P.n (P.tpp of them per pass) from
-// load(t, e) to store(t, e, v), using the padded shared buffers buf + t *
-// stride (t < P.tpp) between stages.  All threads of the CTA must call it.
-// MIXED enables the odd radices; without it only 16, 8 and 4 are compiled,
-// which keeps the power-of-two transforms within the register budget.
-// The caller must synchronise before reusing buf or reading what store wrote
-// to shared memory.
-template <int EPT, bool MIXED, class Load, class Store>
-__device__ __forceinline__ void fft_many(float2 *buf, int stride, int count, const FftPlan &P,
-                                         const float2 *__restrict__ tw, bool inv, int tid, int nthr, Load load,
-                                         Store store) {
-    for (int t0 = 0; t0 < count; t0 += P.tpp) {
-        const int cnt = min(P.tpp, count - t0);
-        auto ld = [&](int t, int e) { return load(t0 + t, e); };
-        auto st = [&](int t, int e, float2 v) { store(t0 + t, e, v); };
-        if (t0 > 0) __syncthreads();
-        int Ns = 1;
-        for (int s = 0; s < P.nstages; ++s) {
-            const int R = P.radix[s];
-            const bool first = s == 0, last = s == P.nstages - 1;
-            switch (R) {
-                case 16: fftdev::stage<16, EPT>(buf, stride, cnt, P.n, Ns, first, last, tw, inv, tid, nthr, ld, st); break;
-                case 8: fftdev::stage<8, EPT>(buf, stride, cnt, P.n, Ns, first, last, tw, inv, tid, nthr, ld, st); break;
-                case 4: fftdev::stage<4, EPT>(buf, stride, cnt, P.n, Ns, first, last, tw, inv, tid, nthr, ld, st); break;
-                default:
-                    if constexpr (MIXED) {
-                        if (R == 7)
-                            fftdev::stage<7, EPT>(buf, stride, cnt, P.n, Ns, first, last, tw, inv, tid, nthr, ld, st);
-                        else if (R == 5)
-                            fftdev::stage<5, EPT>(buf, stride, cnt, P.n, Ns, first, last, tw, inv, tid, nthr, ld, st);
-                        else
-                            fftdev::stage<3, EPT>(buf, stride, cnt, P.n, Ns, first, last, tw, inv, tid, nthr, ld, st);
-                    }
-                    break;
+// Transform COUNT sequences of length P.n from load(t, e) to store(t, e, v)
+// (t < COUNT), using the shared buffers buf + t * P.stride between stages.
+// All threads of the CTA must call it; shared buffers may be reused after the
+// caller's next barrier.  MIXED enables the odd radices (and integer
+// division in the index arithmetic); without it n is a power of two and only
+// radices 16, 8 and 4 are compiled.
+template <bool MIXED, int COUNT, class Load, class Store>
+__device__ __forceinline__ void fft_many(float2 *buf, const FftPlan &P, const float2 *__restrict__ tw, bool inv,
+                                         int tid, int nthr, Load load, Store store) {
+    constexpr bool POW2 = !MIXED;
+    switch (P.radix[0]) {
+        case 16: fftdev::dit_first<16, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store); break;
+        case 8: fftdev::dit_first<8, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store); break;
+        case 4: fftdev::dit_first<4, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store); break;
+        default:
+            if constexpr (MIXED) {
+                if (P.radix[0] == 7) fftdev::dit_first<7, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
+                else if (P.radix[0] == 5) fftdev::dit_first<5, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
+                else fftdev::dit_first<3, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
             }
-            Ns *= R;
+            break;
+    }
+    int L = P.radix[0];
+    for (int s = 1; s < P.nstages; ++s) {
+        const int R = P.radix[s];
+        const bool last = s == P.nstages - 1;
+        switch (R) {
+            case 16: fftdev::dit_stage<16, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store); break;
+            case 8: fftdev::dit_stage<8, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store); break;
+            case 4: fftdev::dit_stage<4, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store); break;
+            default:
+                if constexpr (MIXED) {
+                    if (R == 7) fftdev::dit_stage<7, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store);
+                    else if (R == 5) fftdev::dit_stage<5, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store);
+                    else fftdev::dit_stage<3, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store);
+                }
+                break;
         }
+        L *= R;
     }
 }
 

@@ -10,14 +10,18 @@
 namespace ws {
 
 struct FftPlan {
-    int n;          // transform length
+    int n;            // transform length
     int nstages;
-    int radix[8];   // stage radices, first stage first
-    int tpp;        // transforms handled together per pass (1, 2 or 4)
+    int radix[8];     // stage radices, first stage first
+    int xw[8];        // first-stage digit weights: xw[i] = radix[i+1] * ... * radix[nstages-1]
+    int gw[8];        // position weights: gw[i] = radix[1] * ... * radix[i-1]  (gw[1] = 1)
+    int lxw[8], lgw[8];  // log2 of xw / gw when n is a power of two
+    int logn;         // log2 n when n is a power of two
+    int padshift;     // shared-memory padding: one slot after every 2^padshift elements
+    int stride;       // float2 slots per transform buffer (== 8 mod 16)
 };
 
-// Shared-memory index of element e: one pad slot every 16 elements.
-WS_HD constexpr int fft_pad(int e) { return e + (e >> 4); }
-WS_HD constexpr int fft_padded_len(int n) { return n + (n >> 4) + 1; }
+// Shared-memory index of element e with one pad slot every 2^shift elements.
+WS_HD constexpr int fft_pad(int e, int shift) { return e + (e >> shift); }
 
 }  // namespace ws

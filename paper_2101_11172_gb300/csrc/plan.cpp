@@ -164,8 +164,9 @@ struct StageTimer {
 };
 
 // Radices of an N'-point transform: 16, 8, 4 for the power of two (N' is a
-// multiple of 32, so no radix 2 is needed), then 7, 5, 3.
-bool fft_radices(int n, FftPlan *F) {
+// multiple of 32, so no radix 2 is needed), then 7, 5, 3; plus the digit
+// weights of the first stage's reversal and the shared-memory layout.
+bool fft_make_plan(int n, FftPlan *F) {
     int a = 0, m = n;
     while (m % 2 == 0) {
         m /= 2;
@@ -188,20 +189,30 @@ bool fft_radices(int n, FftPlan *F) {
             F->radix[ns++] = p;
             m /= p;
         }
+    if (m != 1) return false;
     F->n = n;
     F->nstages = ns;
-    return m == 1;
-}
-
-// Transforms per pass for `count` transforms on `nthr` threads within the
-// per-thread register budget of one FFT stage.
-bool fft_variant(FftPlan *F, int count, int nthr) {
-    for (int tpp = count; tpp >= 1; tpp /= 2)
-        if (fft_elements_needed(*F, tpp, nthr) <= fft_elements_budget()) {
-            F->tpp = tpp;
-            return true;
-        }
-    return false;
+    auto log2i = [](int v) {
+        int l = 0;
+        while ((1 << l) < v) ++l;
+        return (1 << l) == v ? l : -1;
+    };
+    for (int i = 0; i < ns; ++i) {
+        int xw = 1, gw = 1;
+        for (int l = i + 1; l < ns; ++l) xw *= F->radix[l];
+        for (int l = 1; l < i; ++l) gw *= F->radix[l];
+        F->xw[i] = xw;
+        F->gw[i] = gw;
+        F->lxw[i] = log2i(xw);
+        F->lgw[i] = log2i(gw);
+    }
+    F->logn = log2i(n);
+    int shift = 4;
+    while ((2 << shift) <= n / F->radix[0]) ++shift;
+    F->padshift = shift;
+    int len = (n - 1) + ((n - 1) >> shift) + 1;
+    F->stride = len + ((8 - len % 16) + 16) % 16;     // == 8 (mod 16)
+    return true;
 }
 
 ws_status finish_call(ws_plan_s *p, cudaStream_t s) {
@@ -323,15 +334,8 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
         delete p;
         return WS_ERR_ARG;
     }
-    if (!fft_radices((int)Np, &p->fft2) || !fft_variant(&p->fft2, fft_per_cta(), fft_threads_pair())) {
-        set_error("ws_plan: no transform plan for N' = " + std::to_string(Np));
-        delete p;
-        return WS_ERR_ARG;
-    }
     p->fft_mixed = (Np & (Np - 1)) != 0;
-    p->fft1 = p->fft2;
-    if (!fft_variant(&p->fft1, 1, fft_threads_one()) ||
-        transform_smem_bytes((int)Np, N) > (size_t)227 * 1024) {
+    if (!fft_make_plan((int)Np, &p->fft) || transform_smem_bytes(p->fft, N) > (size_t)227 * 1024) {
         set_error("ws_plan: no transform plan for N' = " + std::to_string(Np));
         delete p;
         return WS_ERR_ARG;
@@ -413,7 +417,7 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
         WS_TRY(cudaMemcpy(p->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice),
                "uploading twiddles");
     }
-    WS_TRY(setup_transform_kernels((int)Np, N), "configuring transform kernels");
+    WS_TRY(setup_transform_kernels(p->fft, N), "configuring transform kernels");
     WS_TRY(dev_alloc(&p->d_counts, (size_t)p->ntiles + 1, &p->bytes), "allocating tile counts");
     WS_TRY(dev_alloc(&p->d_offsets, (size_t)p->ntiles + 1, &p->bytes), "allocating tile offsets");
     WS_TRY(dev_alloc(&p->d_blocksums, (size_t)4096, &p->bytes), "allocating scan sums");

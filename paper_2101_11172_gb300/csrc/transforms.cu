@@ -24,10 +24,9 @@
 namespace ws {
 namespace {
 
-constexpr int kThreads = 512;       // two rows or two columns per CTA
+constexpr int kThreads = 256;       // two rows or two columns per CTA
 constexpr int kPerCta = 2;
 constexpr int kRowThreads = 256;    // one row per CTA (inv_rows)
-constexpr int kEPT = 16;            // elements a thread holds in one FFT stage
 
 __device__ __forceinline__ int grid_to_crop(int g, int half, int Np) { return g < half ? g + half : g - (Np - half); }
 __device__ __forceinline__ bool in_crop(int g, int half, int Np) { return g < half || g >= Np - half; }
@@ -35,7 +34,7 @@ __device__ __forceinline__ bool in_crop(int g, int half, int Np) { return g < ha
 // -- degridding --------------------------------------------------------------
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ img,
                 const float2 *__restrict__ zsplit, int plane0, float2 *__restrict__ stack) {
     extern __shared__ __align__(16) float2 sbuf[];
@@ -52,11 +51,11 @@ fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
         return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
     };
     auto store = [&](int b, int R, float2 v) { __stcs(plane + tiled_index(ii0 + b, R, Np), v); };
-    fft_many<kEPT, MIXED>(sbuf, fft_padded_len(Np), kPerCta, F, tw, false, threadIdx.x, kThreads, load, store);
+    fft_many<MIXED, kPerCta>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, float2 *__restrict__ stack) {
     extern __shared__ __align__(16) float2 sbuf[];
     const int Np = L.Np, half = L.N / 2;
@@ -68,13 +67,13 @@ fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, float2 *__re
         return __ldcs(blk + (size_t)grid_to_crop(S, half, Np) * CB + b);
     };
     auto store = [&](int b, int S, float2 v) { blk[(size_t)S * CB + b] = v; };
-    fft_many<kEPT, MIXED>(sbuf, fft_padded_len(Np), kPerCta, F, tw, false, threadIdx.x, kThreads, load, store);
+    fft_many<MIXED, kPerCta>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
 }
 
 // -- gridding ----------------------------------------------------------------
 
 template <bool MIXED>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, float2 *__restrict__ stack) {
     extern __shared__ __align__(16) float2 sbuf[];
     const int Np = L.Np, half = L.N / 2;
@@ -85,12 +84,8 @@ inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, float2 *__re
     auto store = [&](int b, int S, float2 v) {
         if (in_crop(S, half, Np)) blk[(size_t)grid_to_crop(S, half, Np) * CB + b] = v;
     };
-    fft_many<kEPT, MIXED>(sbuf, fft_padded_len(Np), kPerCta, F, tw, true, threadIdx.x, kThreads, load, store);
+    fft_many<MIXED, kPerCta>(sbuf, F, tw, true, threadIdx.x, kThreads, load, store);
 }
-
-// float2 slots of one padded row, rounded up to an even count so that the
-// float4 array placed after it (and after the even-length z row) is 16-byte aligned
-__host__ __device__ constexpr int row_slots(int Np) { return (fft_padded_len(Np) + 1) & ~1; }
 
 // One CTA owns image row ii and sums the chunk's planes into a compensated
 // accumulator in shared memory; the last FFT stage screens and accumulates.
@@ -101,7 +96,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 float4 *__restrict__ acc, int first, int last, float2 *__restrict__ dirty) {
     extern __shared__ __align__(16) float2 sbuf[];
     const int Np = L.Np, N = L.N, half = N / 2;
-    float2 *zrow = sbuf + row_slots(Np);                         // N
+    float2 *zrow = sbuf + F.stride;                              // N (F.stride is even: 16-byte aligned)
     float4 *srow = reinterpret_cast<float4 *>(zrow + N);         // N: (sum re, sum im, comp re, comp im)
     const int ii = blockIdx.x;
     const int tid = threadIdx.x;
@@ -126,7 +121,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
             kahan_add(a.y, a.w, v.x * sn + v.y * cs);
             srow[jj] = a;
         };
-        fft_many<kEPT, MIXED>(sbuf, 0, 1, F, tw, true, tid, kRowThreads, load, store);
+        fft_many<MIXED, 1>(sbuf, F, tw, true, tid, kRowThreads, load, store);
         __syncthreads();
     }
     for (int jj = tid; jj < N; jj += kRowThreads) {
@@ -140,9 +135,9 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
     }
 }
 
-size_t smem2(int Np) { return (size_t)kPerCta * fft_padded_len(Np) * sizeof(float2); }
-size_t smem_rows(int Np, int N) {
-    return (size_t)row_slots(Np) * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4));
+size_t smem2(const FftPlan &F) { return (size_t)kPerCta * F.stride * sizeof(float2); }
+size_t smem_rows(const FftPlan &F, int N) {
+    return (size_t)F.stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4));
 }
 
 template <typename K>
@@ -152,27 +147,16 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-// Largest thread-elements need of one stage when `tpp` transforms run together.
-int fft_elements_needed(const FftPlan &F, int tpp, int nthr) {
-    int need = 0;
-    for (int s = 0; s < F.nstages; ++s) {
-        const int R = F.radix[s];
-        const int per = (tpp * (F.n / R) + nthr - 1) / nthr;
-        need = need > per * R ? need : per * R;
-    }
-    return need;
-}
-
-int fft_elements_budget() { return kEPT; }
-int fft_threads_pair() { return kThreads; }
-int fft_threads_one() { return kRowThreads; }
+int fft_threads() { return kThreads; }
 int fft_per_cta() { return kPerCta; }
 
-size_t transform_smem_bytes(int Np, int N) { return smem2(Np) > smem_rows(Np, N) ? smem2(Np) : smem_rows(Np, N); }
+size_t transform_smem_bytes(const FftPlan &F, int N) {
+    return smem2(F) > smem_rows(F, N) ? smem2(F) : smem_rows(F, N);
+}
 
-cudaError_t setup_transform_kernels(int Np, int N) {
+cudaError_t setup_transform_kernels(const FftPlan &F, int N) {
     cudaError_t e;
-    const size_t s2 = smem2(Np), s1 = smem_rows(Np, N);
+    const size_t s2 = smem2(F), s1 = smem_rows(F, N);
     if ((e = allow_smem(fwd_rows_kernel<false>, s2)) != cudaSuccess) return e;
     if ((e = allow_smem(fwd_rows_kernel<true>, s2)) != cudaSuccess) return e;
     if ((e = allow_smem(fwd_cols_kernel<false>, s2)) != cudaSuccess) return e;
@@ -186,45 +170,45 @@ cudaError_t setup_transform_kernels(int Np, int N) {
 
 cudaError_t launch_fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
     const dim3 grid(p->L.N / kPerCta, planes);
-    const size_t smem = smem2(p->L.Np);
+    const size_t smem = smem2(p->fft);
     if (p->fft_mixed)
-        fwd_rows_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_img, p->d_zsplit,
+        fwd_rows_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit,
                                                            chunk * p->P, p->d_stack);
     else
-        fwd_rows_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_img, p->d_zsplit,
+        fwd_rows_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit,
                                                             chunk * p->P, p->d_stack);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_cols(const ws_plan_s *p, int planes, cudaStream_t s) {
     const dim3 grid(p->L.Np / kPerCta, planes);
-    const size_t smem = smem2(p->L.Np);
+    const size_t smem = smem2(p->fft);
     if (p->fft_mixed)
-        fwd_cols_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+        fwd_cols_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_stack);
     else
-        fwd_cols_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+        fwd_cols_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_stack);
     return cudaGetLastError();
 }
 
 cudaError_t launch_inv_cols(const ws_plan_s *p, int planes, cudaStream_t s) {
     const dim3 grid(p->L.Np / kPerCta, planes);
-    const size_t smem = smem2(p->L.Np);
+    const size_t smem = smem2(p->fft);
     if (p->fft_mixed)
-        inv_cols_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+        inv_cols_kernel<true><<<grid, kThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_stack);
     else
-        inv_cols_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft2, p->d_tw, p->d_stack);
+        inv_cols_kernel<false><<<grid, kThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_stack);
     return cudaGetLastError();
 }
 
 cudaError_t launch_inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
                             cudaStream_t s) {
-    const size_t smem = smem_rows(p->L.Np, p->L.N);
+    const size_t smem = smem_rows(p->fft, p->L.N);
     if (p->fft_mixed)
-        inv_rows_kernel<true><<<p->L.N, kRowThreads, smem, s>>>(p->L, p->fft1, p->d_tw, p->d_stack, chunk * p->P,
+        inv_rows_kernel<true><<<p->L.N, kRowThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_stack, chunk * p->P,
                                                                 planes, p->d_zsplit, p->d_corr, p->d_acc, first,
                                                                 last, dirty);
     else
-        inv_rows_kernel<false><<<p->L.N, kRowThreads, smem, s>>>(p->L, p->fft1, p->d_tw, p->d_stack, chunk * p->P,
+        inv_rows_kernel<false><<<p->L.N, kRowThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_stack, chunk * p->P,
                                                                  planes, p->d_zsplit, p->d_corr, p->d_acc, first,
                                                                  last, dirty);
     return cudaGetLastError();

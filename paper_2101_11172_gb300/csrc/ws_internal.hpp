@@ -64,7 +64,7 @@ struct ws_plan_s {
     int P = 0;                     // planes per chunk (multiple of TT)
     float2 *d_stack = nullptr;     // P x N' x N', column-block layout (common.cuh)
     float2 *d_tw = nullptr;        // N' twiddles exp(-2 pi i m / N')
-    ws::FftPlan fft2{}, fft1{};    // two rows / columns per CTA, one row per CTA
+    ws::FftPlan fft{};             // the N'-point plane transform
     bool fft_mixed = false;        // N' has a factor 3, 5 or 7
     // per-call buffers (grow on demand)
     ws::VisRec *d_rec = nullptr;
@@ -106,13 +106,10 @@ cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64
                                 float2 *vis, cudaStream_t s);
 
 // Plane transforms (transforms.cu).
-int fft_elements_needed(const FftPlan &F, int tpp, int nthr);
-int fft_elements_budget();
-int fft_threads_pair();
-int fft_threads_one();
+int fft_threads();
 int fft_per_cta();
-size_t transform_smem_bytes(int Np, int N);
-cudaError_t setup_transform_kernels(int Np, int N);
+size_t transform_smem_bytes(const FftPlan &F, int N);
+cudaError_t setup_transform_kernels(const FftPlan &F, int N);
 cudaError_t launch_fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_fwd_cols(const ws_plan_s *p, int planes, cudaStream_t s);
 cudaError_t launch_inv_cols(const ws_plan_s *p, int planes, cudaStream_t s);
