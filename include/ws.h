@@ -130,6 +130,29 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
 ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
                   void *dirty, ws_stream_t stream);
 
+/* Allocation-free degridding.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory while they run (a
+ * process whose device memory budget is fixed at start-up, a plug-in whose
+ * host application owns every allocation, code that must not trigger the
+ * synchronisation an allocation can imply).  It computes the same result as
+ * ws_degrid, with the same arguments and status codes, but takes all of its
+ * per-call scratch (visibility records, tile lists, the corrected image, the
+ * w-plane chunk) from one 64 MiB array in device memory that the library
+ * holds on every device that loads it, until the process exits.  It calls no
+ * cudaMalloc or cudaFree and allocates nothing else on the device.
+ *   - The plan (made earlier by ws_plan, which does allocate) supplies the
+ *     tables; the caller supplies inputs and outputs as for ws_degrid.
+ *   - Problems whose records, image and at least 8 w-planes of N' x N' do not
+ *     fit in the 64 MiB are rejected with WS_ERR_ARG and a message.
+ *   - The first call on a device looks up the array's device address (a
+ *     runtime symbol query that may load the module); make that first call
+ *     before capturing the stream into a graph.
+ *   - Every call on a device shares the one array: calls whose GPU work
+ *     overlaps (different streams, or different host threads) race and give
+ *     wrong results.  Serialise them. */
+ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const double *uvw, int64_t M,
+                            void *vis, ws_stream_t stream);
+
 /* Visibilities dropped by the plan's latest call (waits for that call). */
 ws_status ws_plan_dropped(ws_plan_t plan, int64_t *dropped);
 

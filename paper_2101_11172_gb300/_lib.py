@@ -21,8 +21,8 @@ STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_ARG", 2: "WS_ERR_UV_RANGE", 3: "WS_ERR_W_
                 4: "WS_ERR_CUDA", 5: "WS_ERR_OOM", 6: "WS_ERR_TIMEOUT"}
 
 # every entry point declared in include/ws.h
-EXPORTS = ("ws_plan", "ws_degrid", "ws_grid", "ws_plan_dropped", "ws_plan_info", "ws_plan_stats",
-           "ws_destroy", "ws_last_error")
+EXPORTS = ("ws_plan", "ws_degrid", "ws_grid", "ws_degrid_noalloc", "ws_plan_dropped", "ws_plan_info",
+           "ws_plan_stats", "ws_destroy", "ws_last_error")
 
 
 class PlanInfo(ctypes.Structure):
@@ -64,6 +64,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
     lib.ws_plan.argtypes = [ctypes.POINTER(vp), i32, dbl, i32, dbl, dbl, dbl, u32]
     lib.ws_degrid.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_grid.argtypes = [vp, vp, vp, i64, vp, vp]
+    lib.ws_degrid_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_plan_dropped.argtypes = [vp, ctypes.POINTER(i64)]
     lib.ws_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     lib.ws_plan_stats.argtypes = [vp, ctypes.POINTER(Stats), i32]
@@ -100,6 +101,14 @@ def ws_degrid(plan: int, image_ptr: int, uvw_ptr: int, M: int, vis_ptr: int, str
 
 def ws_grid(plan: int, uvw_ptr: int, vis_ptr: int, M: int, dirty_ptr: int, stream: int = 0) -> int:
     st = load().ws_grid(plan, uvw_ptr, vis_ptr, M, dirty_ptr, stream)
+    if st not in (WS_OK, WS_ERR_UV_RANGE, WS_ERR_W_RANGE):
+        _check(st)
+    return st
+
+
+def ws_degrid_noalloc(plan: int, image_ptr: int, uvw_ptr: int, M: int, vis_ptr: int, stream: int = 0) -> int:
+    """Degridding with no device allocation (scratch in a fixed 64 MiB device array)."""
+    st = load().ws_degrid_noalloc(plan, image_ptr, uvw_ptr, M, vis_ptr, stream)
     if st not in (WS_OK, WS_ERR_UV_RANGE, WS_ERR_W_RANGE):
         _check(st)
     return st
