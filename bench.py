@@ -174,18 +174,29 @@ def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int,
     return None
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if the source is unchanged."""
+def library_source_sha() -> str:
+    """Hash of every CUDA/C++ source of the library (any kernel change invalidates counters)."""
+    import glob
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2101_11172_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".hpp", ".cpp")):
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_for(stage: str, planes: int):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
+    scaled to this launch's planes; None if the sources changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             data = json.load(f)
-        src = os.path.join(ROOT, "paper_2101_11172_gb300", "csrc", "wstack.cu")
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        ent = data.get(kernel)
-        if ent and ent.get("source_sha256") == sha:
-            return ent.get("dram_bytes_per_launch_full")
-    except (OSError, ValueError):
+        ent = data.get(stage)
+        if ent and data.get("source_sha256") == library_source_sha() and "planes_profile" in ent \
+                and "dram_bytes_per_launch_full" in ent:
+            return int(ent["dram_bytes_per_launch_profile"] / ent["planes_profile"] * planes)
+    except (OSError, ValueError, KeyError):
         pass
     return None
 
@@ -438,7 +449,7 @@ def main():
     d = stages[dom]
     roof = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
             "frac": None if d["gbs"] is None else d["gbs"] / peak, "peak_source": peak_src,
-            "traffic": traffic_for(dom)}
+            "traffic": traffic_for(dom, total_planes // nchunks)}
     acc = {} if args.no_accuracy else accuracy_sample(wl, vout.cpu().numpy().astype(np.complex128),
                                                        dout.cpu().numpy().astype(np.complex128))
     cpu = None
