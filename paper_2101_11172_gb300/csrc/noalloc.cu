@@ -6,8 +6,8 @@
 // device allocations) or code that must not trigger the implicit device
 // synchronisation an allocation can cause.  For them this file runs the same
 // degridding kernels as ws_degrid, but takes every per-call scratch buffer
-// (visibility records, tile lists and counts, the corrected image, the
-// w-plane chunk and the drop counters) from one fixed, file-scope device
+// (visibility records, tile lists, counts and occupancy, the corrected
+// image, the w-plane chunk and the drop counters) from one fixed, file-scope device
 // array instead of the plan's workspace.  The plan itself (tables made by
 // ws_plan) and the caller's inputs and outputs are used as they are.
 #include <cuda_runtime.h>
@@ -90,6 +90,8 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
     uint32_t *offsets = reinterpret_cast<uint32_t *>(take((size_t)(p->ntiles + 1) * sizeof(uint32_t)));
     uint32_t *blocksums = reinterpret_cast<uint32_t *>(take(4096 * sizeof(uint32_t)));
     unsigned long long *drop = reinterpret_cast<unsigned long long *>(take(2 * sizeof(unsigned long long)));
+    uint8_t *tile_occ = take((size_t)p->ntiles);
+    uint8_t *col_occ = take((size_t)p->L.ntt * p->L.ntu);
     float2 *img = reinterpret_cast<float2 *>(take(n_img * sizeof(float2)));
     if (off > kScratchBytes || (kScratchBytes - off) / plane < (size_t)TT) {
         set_error("ws_degrid_noalloc: the problem needs more than the 64 MiB of fixed scratch (visibility "
@@ -123,6 +125,8 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
     v.d_blocksums = blocksums;
     v.d_img = img;
     v.d_drop = drop;
+    v.d_tile_occ = tile_occ;
+    v.d_col_occ = col_occ;
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(drop, 0, 2 * sizeof(unsigned long long), s);
@@ -134,6 +138,8 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
             return cuda_fail(e, "ws_degrid_noalloc: prep kernel");
         if ((e = launch_bin(&v, M, false, s)) != cudaSuccess)
             return cuda_fail(e, "ws_degrid_noalloc: binning kernels");
+        if ((e = launch_mark(&v, M, s)) != cudaSuccess)
+            return cuda_fail(e, "ws_degrid_noalloc: occupancy kernel");
         if ((e = launch_correct_image(&v, static_cast<const float2 *>(image), s)) != cudaSuccess)
             return cuda_fail(e, "ws_degrid_noalloc: correction kernel");
         const int nchunks = (total + P - 1) / P;
@@ -141,7 +147,7 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
             const int planes = std::min(P, total - c * P);
             if ((e = launch_fwd_rows(&v, c, planes, s)) != cudaSuccess)
                 return cuda_fail(e, "ws_degrid_noalloc: fwd_rows kernel");
-            if ((e = launch_fwd_cols(&v, planes, s)) != cudaSuccess)
+            if ((e = launch_fwd_cols(&v, c, planes, s)) != cudaSuccess)
                 return cuda_fail(e, "ws_degrid_noalloc: fwd_cols kernel");
             if ((e = launch_degrid_chunk(&v, c, planes, M, static_cast<float2 *>(vis), s)) != cudaSuccess)
                 return cuda_fail(e, "ws_degrid_noalloc: degrid3d kernel");

@@ -84,6 +84,8 @@ void release(ws_plan_s *p) {
     cudaFree(p->d_offsets);
     cudaFree(p->d_blocksums);
     cudaFree(p->d_acc);
+    cudaFree(p->d_tile_occ);
+    cudaFree(p->d_col_occ);
     cudaFree(p->d_img);
     cudaFree(p->d_drop);
     if (p->h_drop) cudaFreeHost(p->h_drop);
@@ -422,6 +424,8 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
     WS_TRY(dev_alloc(&p->d_offsets, (size_t)p->ntiles + 1, &p->bytes), "allocating tile offsets");
     WS_TRY(dev_alloc(&p->d_blocksums, (size_t)4096, &p->bytes), "allocating scan sums");
     WS_TRY(dev_alloc(&p->d_acc, (size_t)N * N, &p->bytes), "allocating the accumulator");
+    WS_TRY(dev_alloc(&p->d_tile_occ, (size_t)p->ntiles, &p->bytes), "allocating tile occupancy");
+    WS_TRY(dev_alloc(&p->d_col_occ, (size_t)L.ntt * L.ntu, &p->bytes), "allocating strip occupancy");
     WS_TRY(dev_alloc(&p->d_img, (size_t)N * N, &p->bytes), "allocating the corrected image");
     WS_TRY(dev_alloc(&p->d_drop, (size_t)2, &p->bytes), "allocating drop counters");
     WS_TRY(cudaMallocHost((void **)&p->h_drop, 2 * sizeof(unsigned long long)), "allocating pinned counters");
@@ -459,8 +463,9 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
             return cuda_fail(e, "ws_grid: prep kernel");
     }
     {
-        StageTimer t(p, s, WS_STAGE_BIN, M > 0 ? 5 : 3);
+        StageTimer t(p, s, WS_STAGE_BIN, M > 0 ? 6 : 3);
         if ((e = launch_bin(p, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: binning kernels");
+        if ((e = launch_mark(p, M, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy kernel");
     }
     const int total = p->L.ntt * TT;
     const int nchunks = (total + p->P - 1) / p->P;
@@ -473,7 +478,8 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
         }
         {
             StageTimer t(p, s, WS_STAGE_COLS_INV, 1);
-            if ((e = launch_inv_cols(p, planes, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: inv_cols kernel");
+            if ((e = launch_inv_cols(p, c, planes, s)) != cudaSuccess)
+                return cuda_fail(e, "ws_grid: inv_cols kernel");
         }
         {
             StageTimer t(p, s, WS_STAGE_ROWS_INV, 1);
@@ -512,8 +518,9 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
             return cuda_fail(e, "ws_degrid: prep kernel");
     }
     {
-        StageTimer t(p, s, WS_STAGE_BIN, 5);
+        StageTimer t(p, s, WS_STAGE_BIN, 6);
         if ((e = launch_bin(p, M, false, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: binning kernels");
+        if ((e = launch_mark(p, M, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy kernel");
     }
     {
         StageTimer t(p, s, WS_STAGE_CORRECT, 1);
@@ -531,7 +538,8 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
         }
         {
             StageTimer t(p, s, WS_STAGE_COLS_FWD, 1);
-            if ((e = launch_fwd_cols(p, planes, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: fwd_cols kernel");
+            if ((e = launch_fwd_cols(p, c, planes, s)) != cudaSuccess)
+                return cuda_fail(e, "ws_degrid: fwd_cols kernel");
         }
         {
             StageTimer t(p, s, WS_STAGE_DEGRID3D, 1);

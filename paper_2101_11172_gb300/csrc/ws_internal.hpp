@@ -75,6 +75,8 @@ struct ws_plan_s {
     uint32_t *d_offsets = nullptr; // ntiles + 1
     uint32_t *d_blocksums = nullptr;
     int64_t ntiles = 0;
+    uint8_t *d_tile_occ = nullptr; // ntiles: 1 if any visibility footprint touches the tile
+    uint8_t *d_col_occ = nullptr;  // ntt x ntu: 1 if any tile of that (t-tile, u-tile) strip is touched
     float4 *d_acc = nullptr;       // N x N: (sum re, sum im, comp re, comp im)
     float2 *d_img = nullptr;       // N x N: corrected image (degridding)
     unsigned long long *d_drop = nullptr;   // [0] = non-finite uv, [1] = w out of range
@@ -100,6 +102,7 @@ ws_status cuda_fail(cudaError_t e, const char *what);
 cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,
                         bool grid, cudaStream_t s);
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
+cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s);
 cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s);
 cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64_t M,
@@ -111,8 +114,8 @@ int fft_per_cta();
 size_t transform_smem_bytes(const FftPlan &F, int N);
 cudaError_t setup_transform_kernels(const FftPlan &F, int N);
 cudaError_t launch_fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
-cudaError_t launch_fwd_cols(const ws_plan_s *p, int planes, cudaStream_t s);
-cudaError_t launch_inv_cols(const ws_plan_s *p, int planes, cudaStream_t s);
+cudaError_t launch_fwd_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
+cudaError_t launch_inv_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
                             cudaStream_t s);
 

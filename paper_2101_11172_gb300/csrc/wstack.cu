@@ -153,6 +153,25 @@ __global__ void scatter_kernel(Launch L, const VisRec *__restrict__ rec, int64_t
     for (int i = 0; i < n; ++i) list[offsets[keys[i]] + atomicAdd(&fill[keys[i]], 1u)] = (uint32_t)k;
 }
 
+// Occupancy of the stack: which gridding tiles, and which (t-tile, u-tile)
+// strips of N' rows, any visibility footprint touches.  Every other cell of
+// the stack is zero when gridding and never read when degridding, so the
+// plane kernels skip it.  Plain byte stores of 1 (idempotent, no atomics),
+// each preceded by a load so that the many visibilities sharing a tile do
+// not all write it.
+__global__ void mark_kernel(Launch L, const VisRec *__restrict__ rec, int64_t M, uint8_t *__restrict__ tile_occ,
+                            uint8_t *__restrict__ col_occ) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    uint32_t keys[kMaxKeys];
+    int n = record_keys<true>(L, rec[k], keys);
+    for (int i = 0; i < n; ++i) {
+        if (!tile_occ[keys[i]]) tile_occ[keys[i]] = 1;
+        const uint32_t c = (keys[i] / (L.ntu * L.ntv)) * L.ntu + keys[i] % L.ntu;
+        if (!col_occ[c]) col_occ[c] = 1;
+    }
+}
+
 // Exclusive scan of n uint32 (n <= 4096 * 4096): per-block scan of 4096
 // elements, scan of the block sums in one block, then add back.
 constexpr int kScanThreads = 1024;
@@ -231,6 +250,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     __shared__ float sim[kTileCells];
     __shared__ float swt[kGridThreads / 32][3 * kMaxW];
     const uint32_t tile = tile_base + blockIdx.x;
+    if (offsets[tile] == offsets[tile + 1]) return;   // empty tile: the transforms treat it as zero
     const int tu = tile % L.ntu;
     const int tv = (tile / L.ntu) % L.ntv;
     const int tt = tile / (L.ntu * L.ntv);
@@ -379,6 +399,15 @@ cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s) {
     else
         scatter_kernel<false><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_offsets,
                                                                 p->d_counts, p->d_list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p->d_tile_occ, 0, (size_t)p->ntiles, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
+    if (e != cudaSuccess || M == 0) return e;
+    mark_kernel<<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_tile_occ, p->d_col_occ);
     return cudaGetLastError();
 }
 
