@@ -276,4 +276,108 @@ __device__ __forceinline__ void fft_many(float2 *buf, const FftPlan &P, const fl
     }
 }
 
+// -- compile-time plans for the power-of-two sizes -----------------------------
+//
+// For N' = 512, 1024, 2048 and 4096 the radix sequence, the digit weights of
+// the first stage, the padding and every stride are constants, so each padded
+// shared-memory address is one base plus an immediate offset and each
+// twiddle index is one multiply.  The layout and the arithmetic are those of
+// the runtime engine above (same stride and padding), only specialised.
+
+namespace fftst {
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+template <int N> struct Radices;
+template <> struct Radices<4096> { static constexpr int n = 3, r0 = 16, r1 = 16, r2 = 16; };
+template <> struct Radices<2048> { static constexpr int n = 3, r0 = 16, r1 = 16, r2 = 8; };
+template <> struct Radices<1024> { static constexpr int n = 3, r0 = 16, r1 = 8, r2 = 8; };
+template <> struct Radices<512> { static constexpr int n = 3, r0 = 16, r1 = 8, r2 = 4; };
+
+template <int N> struct Layout {
+    static constexpr int shift = ilog2(N / Radices<N>::r0) < 4 ? 4 : ilog2(N / Radices<N>::r0);
+    static constexpr int len = (N - 1) + ((N - 1) >> shift) + 1;
+    static constexpr int stride = len + ((8 - len % 16) + 16) % 16;
+    __host__ __device__ static constexpr int pad(int e) { return e + (e >> shift); }
+};
+
+// First stage (radix R0): inputs m*(N/R0) + j, outputs to digit-reversed g*R0 + m.
+template <int N, int COUNT, class Load>
+__device__ __forceinline__ void first(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
+                                      Load &load) {
+    using Rd = Radices<N>;
+    using Ly = Layout<N>;
+    constexpr int R = Rd::r0, nb = N / R, total = COUNT * nb;
+    // j = d1 * r2 + d2 (x-order); g = d1 + d2 * r1 (position order)
+    for (int q = tid; q < total; q += nthr) {
+        const int t = q % COUNT, j = q / COUNT;
+        float2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = load(t, m * nb + j);
+        fftdev::dft<R>(v, inv, tw, N);
+        const int d1 = j >> ilog2(Rd::r2), d2 = j & (Rd::r2 - 1);
+        const int g = d1 + d2 * Rd::r1;
+        float2 *x = buf + t * Ly::stride + Ly::pad(g * R);     // R divides 2^shift: one base
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = v[m];
+    }
+    __syncthreads();
+}
+
+// Later stage of radix R over span L (constant): in place, or to store() if LAST.
+template <int N, int COUNT, int R, int L, bool LAST, class Store>
+__device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
+                                      Store &store) {
+    using Ly = Layout<N>;
+    constexpr int nb = N / R, total = COUNT * nb;
+    constexpr int lgL = ilog2(L), lgtw = ilog2(N / (R * L));
+    // pad(base + m L) with base = blk R L + k, k < L, is pad_base + m * step when
+    //  (a) L is a multiple of 2^shift (the pad of m L is exact), or
+    //  (b) R L divides 2^shift ((blk R L + k + m L) >> shift = (blk R L) >> shift);
+    // otherwise each element is padded on its own.
+    constexpr bool wide = (L >> Ly::shift) > 0;
+    constexpr bool inblock = (R * L) <= (1 << Ly::shift);
+    constexpr bool affine = wide || inblock;
+    constexpr int step = wide ? L + (L >> Ly::shift) : L;
+    auto at = [&](int pbase, int base, int m) {
+        return affine ? pbase + m * step : Ly::pad(base + m * L);
+    };
+    for (int q = tid; q < total; q += nthr) {
+        const int t = q % COUNT, bq = q / COUNT;
+        const int blk = bq >> lgL, k = bq & (L - 1);
+        const int base = blk * R * L + k;
+        const int pbase = wide ? Ly::pad(base) : base + ((blk * R * L) >> Ly::shift);
+        float2 *x = buf + t * Ly::stride;
+        float2 v[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = x[at(pbase, base, m)];
+        if (k > 0) {
+#pragma unroll
+            for (int m = 1; m < R; ++m) v[m] = fftdev::cmul(v[m], fftdev::twiddle(tw, (k * m) << lgtw, inv));
+        }
+        fftdev::dft<R>(v, inv, tw, N);
+        if constexpr (LAST) {
+#pragma unroll
+            for (int m = 0; m < R; ++m) store(t, base + m * L, v[m]);
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m) x[at(pbase, base, m)] = v[m];
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+}
+
+}  // namespace fftst
+
+// COUNT transforms of the compile-time size N (see fft_many for the contract).
+template <int N, int COUNT, class Load, class Store>
+__device__ __forceinline__ void fft_static(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
+                                           Load load, Store store) {
+    using Rd = fftst::Radices<N>;
+    static_assert(Rd::n == 3, "three-stage plans only");
+    fftst::first<N, COUNT>(buf, tw, inv, tid, nthr, load);
+    fftst::later<N, COUNT, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store);
+    fftst::later<N, COUNT, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store);
+}
+
 }  // namespace ws

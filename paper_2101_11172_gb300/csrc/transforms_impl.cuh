@@ -1,0 +1,245 @@
+// Kernel templates of the fused plane transforms (see transforms.cu).
+//
+// NP selects the FFT code: 0 = runtime plan, power of two; 1 = runtime plan
+// with odd radices; 512, 1024, 2048, 4096 = the compile-time plans of
+// fft.cuh.  Each translation unit instantiates Transforms<NP> for its sizes.
+#pragma once
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "ws_internal.hpp"
+
+namespace ws {
+namespace tf {
+
+constexpr int kThreads = 256;       // two rows or two columns per CTA
+constexpr int kPerCta = 2;
+constexpr int kRowThreads = 256;    // one row per CTA (inv_rows)
+
+__device__ __forceinline__ int grid_to_crop(int g, int half, int Np) { return g < half ? g + half : g - (Np - half); }
+__device__ __forceinline__ bool in_crop(int g, int half, int Np) { return g < half || g >= Np - half; }
+
+template <int NP, int COUNT, class Load, class Store>
+__device__ __forceinline__ void plane_fft(float2 *buf, const FftPlan &F, const float2 *__restrict__ tw, bool inv,
+                                          int tid, int nthr, Load load, Store store) {
+    if constexpr (NP == 0)
+        fft_many<false, COUNT>(buf, F, tw, inv, tid, nthr, load, store);
+    else if constexpr (NP == 1)
+        fft_many<true, COUNT>(buf, F, tw, inv, tid, nthr, load, store);
+    else
+        fft_static<NP, COUNT>(buf, tw, inv, tid, nthr, load, store);
+}
+
+// -- degridding --------------------------------------------------------------
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 2)
+fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ img,
+                const float2 *__restrict__ zsplit, const uint8_t *__restrict__ col_occ, int plane0,
+                float2 *__restrict__ stack) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, N = L.N, half = N / 2;
+    const int ii0 = blockIdx.x * kPerCta;
+    const int pl = plane0 + (int)blockIdx.y;                     // blockIdx is unsigned: convert first
+    const float t = (float)(pl + L.t_lo);
+    float2 *plane = stack + (size_t)blockIdx.y * Np * Np;
+    // columns of this plane's t-tile that any footprint touches (the others are never read)
+    uint8_t *occ = reinterpret_cast<uint8_t *>(sbuf + kPerCta * F.stride);
+    for (int i = threadIdx.x; i < L.ntu; i += kThreads) occ[i] = col_occ[(pl / TT) * L.ntu + i];
+    __syncthreads();
+    auto load = [&](int b, int J) -> float2 {
+        if (!in_crop(J, half, Np)) return make_float2(0.f, 0.f);
+        const size_t pix = (size_t)(ii0 + b) * N + grid_to_crop(J, half, Np);
+        const float2 g = __ldg(img + pix);
+        float sn, cs;
+        phase_tz(t, __ldg(zsplit + pix), &sn, &cs);          // times exp(-i phi)
+        return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+    };
+    auto store = [&](int b, int R, float2 v) {
+        if (occ[R / TU]) __stcs(plane + tiled_index(ii0 + b, R, Np), v);
+    };
+    plane_fft<NP, kPerCta>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 2)
+fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_t *__restrict__ tile_occ,
+                const uint8_t *__restrict__ col_occ, int plane0, float2 *__restrict__ stack) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, half = L.N / 2;
+    const int R0 = blockIdx.x * kPerCta;                  // two of the four columns of a block
+    const int tt = (plane0 + (int)blockIdx.y) / TT, tu = R0 / TU;
+    if (!col_occ[tt * L.ntu + tu]) return;                // no visibility reads these columns of this plane
+    float2 *blk = stack + (size_t)blockIdx.y * Np * Np + (size_t)(R0 >> 2) * Np * CB + (R0 & 3);
+    uint8_t *occ = reinterpret_cast<uint8_t *>(sbuf + kPerCta * F.stride);
+    for (int i = threadIdx.x; i < L.ntv; i += kThreads) occ[i] = tile_occ[((size_t)tt * L.ntv + i) * L.ntu + tu];
+    __syncthreads();
+    // rows 0..N-1 hold the N transformed image rows; every other row is zero padding
+    auto load = [&](int b, int S) -> float2 {
+        if (!in_crop(S, half, Np)) return make_float2(0.f, 0.f);
+        return __ldcs(blk + (size_t)grid_to_crop(S, half, Np) * CB + b);
+    };
+    auto store = [&](int b, int S, float2 v) {
+        if (occ[S / TV]) blk[(size_t)S * CB + b] = v;     // only tiles the gather reads
+    };
+    plane_fft<NP, kPerCta>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
+}
+
+// -- gridding ----------------------------------------------------------------
+
+template <int NP>
+__global__ void __launch_bounds__(kThreads, 2)
+inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_t *__restrict__ tile_occ,
+                const uint8_t *__restrict__ col_occ, int plane0, float2 *__restrict__ stack) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, half = L.N / 2;
+    const int R0 = blockIdx.x * kPerCta;
+    const int tt = (plane0 + (int)blockIdx.y) / TT, tu = R0 / TU;
+    if (!col_occ[tt * L.ntu + tu]) return;                // all-zero columns: inv_rows skips them too
+    float2 *blk = stack + (size_t)blockIdx.y * Np * Np + (size_t)(R0 >> 2) * Np * CB + (R0 & 3);
+    uint8_t *occ = reinterpret_cast<uint8_t *>(sbuf + kPerCta * F.stride);
+    for (int i = threadIdx.x; i < L.ntv; i += kThreads) occ[i] = tile_occ[((size_t)tt * L.ntv + i) * L.ntu + tu];
+    __syncthreads();
+    // gridding wrote only occupied tiles; every other cell is zero
+    auto load = [&](int b, int S) -> float2 {
+        return occ[S / TV] ? __ldcs(blk + (size_t)S * CB + b) : make_float2(0.f, 0.f);
+    };
+    // keep the N crop rows, compacted into rows 0..N-1 (all reads precede these writes)
+    auto store = [&](int b, int S, float2 v) {
+        if (in_crop(S, half, Np)) blk[(size_t)grid_to_crop(S, half, Np) * CB + b] = v;
+    };
+    plane_fft<NP, kPerCta>(sbuf, F, tw, true, threadIdx.x, kThreads, load, store);
+}
+
+// One CTA owns image row ii and sums the chunk's planes into a compensated
+// accumulator in shared memory; the last FFT stage screens and accumulates.
+template <int NP>
+__global__ void __launch_bounds__(kRowThreads, 2)
+inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ stack,
+                const uint8_t *__restrict__ col_occ, int plane0, int planes, const float2 *__restrict__ zsplit,
+                const float *__restrict__ corr, float4 *__restrict__ acc, int first, int last,
+                float2 *__restrict__ dirty) {
+    extern __shared__ __align__(16) float2 sbuf[];
+    const int Np = L.Np, N = L.N, half = N / 2;
+    float2 *zrow = sbuf + F.stride;                              // N (F.stride is even: 16-byte aligned)
+    float4 *srow = reinterpret_cast<float4 *>(zrow + N);         // N: (sum re, sum im, comp re, comp im)
+    uint8_t *occ = reinterpret_cast<uint8_t *>(srow + N);        // ntu: strips of the current t-tile
+    int occ_tt = -1;
+    const int ii = blockIdx.x;
+    const int tid = threadIdx.x;
+    const size_t pix0 = (size_t)ii * N;
+    for (int jj = tid; jj < N; jj += kRowThreads) {
+        zrow[jj] = zsplit[pix0 + jj];
+        srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
+    }
+    __syncthreads();
+    const int nvalid = min(planes, L.Nw - plane0);
+    for (int p = 0; p < nvalid; ++p) {
+        const float2 *plane = stack + (size_t)p * Np * Np;
+        const float t = (float)(plane0 + p + L.t_lo);
+        const int tt = (plane0 + p) / TT;
+        if (tt != occ_tt) {                  // uniform across the CTA; the previous plane ended with a barrier
+            for (int i = tid; i < L.ntu; i += kRowThreads) occ[i] = col_occ[tt * L.ntu + i];
+            __syncthreads();
+            occ_tt = tt;
+        }
+        // column strips no footprint touched were never transformed: they are zero
+        auto load = [&](int, int R) -> float2 {
+            return occ[R / TU] ? __ldcs(plane + tiled_index(ii, R, Np)) : make_float2(0.f, 0.f);
+        };
+        auto store = [&](int, int J, float2 v) {
+            if (!in_crop(J, half, Np)) return;
+            const int jj = grid_to_crop(J, half, Np);
+            float sn, cs;
+            phase_tz(t, zrow[jj], &sn, &cs);
+            float4 a = srow[jj];
+            kahan_add(a.x, a.z, v.x * cs - v.y * sn);
+            kahan_add(a.y, a.w, v.x * sn + v.y * cs);
+            srow[jj] = a;
+        };
+        plane_fft<NP, 1>(sbuf, F, tw, true, tid, kRowThreads, load, store);
+        __syncthreads();
+    }
+    for (int jj = tid; jj < N; jj += kRowThreads) {
+        const float4 a = srow[jj];
+        if (last) {
+            const float h = corr[pix0 + jj];
+            dirty[pix0 + jj] = make_float2(h * (a.x - a.z), h * (a.y - a.w));
+        } else {
+            acc[pix0 + jj] = a;
+        }
+    }
+}
+
+// transform buffers + one occupancy byte per strip (at most N'/16 or N'/32 of them)
+
+// transform buffers + one occupancy byte per strip (at most N'/16 or N'/32 of them)
+inline size_t smem2(const FftPlan &F) { return (size_t)kPerCta * F.stride * sizeof(float2) + F.n / TU + 16; }
+inline size_t smem_rows(const FftPlan &F, int N) {
+    return (size_t)F.stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4)) + F.n / TU + 16;
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Launchers of one FFT variant.
+template <int NP>
+struct Transforms {
+    static cudaError_t setup(const FftPlan &F, int N) {
+        cudaError_t e;
+        if ((e = allow_smem(fwd_rows_kernel<NP>, smem2(F))) != cudaSuccess) return e;
+        if ((e = allow_smem(fwd_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
+        if ((e = allow_smem(inv_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
+        return allow_smem(inv_rows_kernel<NP>, smem_rows(F, N));
+    }
+    static cudaError_t fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
+        fwd_rows_kernel<NP><<<dim3(p->L.N / kPerCta, planes), kThreads, smem2(p->fft), s>>>(
+            p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit, p->d_col_occ, chunk * p->P, p->d_stack);
+        return cudaGetLastError();
+    }
+    static cudaError_t fwd_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
+        fwd_cols_kernel<NP><<<dim3(p->L.Np / kPerCta, planes), kThreads, smem2(p->fft), s>>>(
+            p->L, p->fft, p->d_tw, p->d_tile_occ, p->d_col_occ, chunk * p->P, p->d_stack);
+        return cudaGetLastError();
+    }
+    static cudaError_t inv_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
+        inv_cols_kernel<NP><<<dim3(p->L.Np / kPerCta, planes), kThreads, smem2(p->fft), s>>>(
+            p->L, p->fft, p->d_tw, p->d_tile_occ, p->d_col_occ, chunk * p->P, p->d_stack);
+        return cudaGetLastError();
+    }
+    static cudaError_t inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
+                                cudaStream_t s) {
+        inv_rows_kernel<NP><<<p->L.N, kRowThreads, smem_rows(p->fft, p->L.N), s>>>(
+            p->L, p->fft, p->d_tw, p->d_stack, p->d_col_occ, chunk * p->P, planes, p->d_zsplit, p->d_corr,
+            p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty);
+        return cudaGetLastError();
+    }
+};
+
+// Entry points of one variant, exported by the translation unit that
+// instantiates it (so every kernel is compiled exactly once).
+struct Ops {
+    cudaError_t (*setup)(const FftPlan &, int);
+    cudaError_t (*fwd_rows)(const ws_plan_s *, int, int, cudaStream_t);
+    cudaError_t (*fwd_cols)(const ws_plan_s *, int, int, cudaStream_t);
+    cudaError_t (*inv_cols)(const ws_plan_s *, int, int, cudaStream_t);
+    cudaError_t (*inv_rows)(const ws_plan_s *, int, int, bool, bool, float2 *, cudaStream_t);
+};
+
+template <int NP>
+constexpr Ops ops_of() {
+    return Ops{&Transforms<NP>::setup, &Transforms<NP>::fwd_rows, &Transforms<NP>::fwd_cols,
+               &Transforms<NP>::inv_cols, &Transforms<NP>::inv_rows};
+}
+
+const Ops &ops_runtime_pow2();
+const Ops &ops_runtime_mixed();
+const Ops &ops_512();
+const Ops &ops_1024();
+const Ops &ops_2048();
+const Ops &ops_4096();
+
+}  // namespace tf
+}  // namespace ws
