@@ -160,3 +160,34 @@ def survey_slab(w_half: float = 35.0, **kw) -> Workload:
     sel = abs(wl.uvw[:, 2]) < w_half
     return Workload(f"survey-slab-N{wl.N}-w{w_half:g}", wl.N, wl.x0, wl.W, wl.fov, wl.uvw[sel], wl.image,
                     wl.vis[sel])
+
+
+@dataclass
+class Chi2Workload(Workload):
+    """A chi^2 imaging problem: ``image`` is the true (real) sky, ``vis`` the
+    noise added to its visibilities, ``estimate`` the (real) image at which
+    chi^2 and its gradient are evaluated."""
+    sigma: float = 0.01
+    estimate: np.ndarray = field(default=None, repr=False)
+
+
+def differentiable(N: int = 1024, n_ant: int = 256, n_times: int = 61, fov: float = 0.5, W: int = 7,
+                   x0: float = 0.25, sigma: float = 0.01, n_src: int = 200, index: int = 3) -> Chi2Workload:
+    """Differentiable-imaging workload: chi^2 between degridded and target visibilities.
+
+    Image 1024 x 1024 (grid 2048), the survey array (256 antennas in a 10 km
+    disc, dec -30, 8 h) sampled 61 times: 32,640 x 61 = 1,991,040
+    visibilities, max |(u,v)| = 0.45 N / fov.  True sky: 200 point sources
+    with amplitudes U(0.1, 1); target noise CN(0, sigma^2).  The estimate is
+    the true sky with each amplitude scaled by U(0.7, 1.3) plus 20 spurious
+    sources with amplitudes U(0.05, 0.3).  Both images are real.
+    """
+    uvw = array_uvw(n_ant, 10_000.0, -30.0, -30.0, (-4.0, 4.0), n_times, 0.45 * N / fov, rng_for(index, 1))
+    sky = point_sky(N, n_src, rng_for(index, 2)).real.copy()
+    noise = complex_normal(uvw.shape[0], rng_for(index, 4), sigma)
+    r = rng_for(index, 5)
+    rows, cols = np.nonzero(sky)
+    est = np.zeros_like(sky)
+    est[rows, cols] = sky[rows, cols] * r.uniform(0.7, 1.3, rows.size)
+    est += point_sky(N, 20, r, 0.05, 0.3).real
+    return Chi2Workload(f"chi2-N{N}-M{uvw.shape[0]}", N, x0, W, fov, uvw, sky, noise, sigma=sigma, estimate=est)
