@@ -148,7 +148,7 @@ def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int,
     column transform reads it and writes back the N crop rows (cols_inv);
     the row transform reads those rows and, once per chunk, the running sum
     (rows_inv).  Degridding mirrors it: the row transform reads the image and
-    z and writes N rows (rows_fwd); the column transform reads them and writes
+    z once per chunk and writes N rows per plane (rows_fwd); the column transform reads them and writes
     the full plane (cols_fwd).  Records are 32 B per visibility.  Stages that
     run once per plane chunk divide by the chunk count.
     """
@@ -162,7 +162,7 @@ def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int,
     if stage == "rows_inv":
         return planes * crop + N * N * (8 + 16 + 16 + 4 + 8)
     if stage == "rows_fwd":
-        return planes * (N * N * 16 + crop)
+        return N * N * 16 + planes * crop
     if stage == "cols_fwd":
         return planes * (crop + full)
     if stage == "degrid3d":

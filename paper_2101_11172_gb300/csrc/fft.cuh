@@ -324,6 +324,41 @@ __device__ __forceinline__ void first(float2 *buf, const float2 *__restrict__ tw
     __syncthreads();
 }
 
+// v[m] *= w^m for m = 1..R-1, w = exp(-+ 2 pi i e / n).  The table holds w^m
+// to half an ulp, but a warp's loads of w^m for m > 1 scatter over many
+// sectors; so only w and w^4 are read and the other powers are products of
+// them (at most five roundings: RMS error about 7e-8 against 2e-8 for the
+// table, far below the FP32 transform's own rounding).
+template <int R>
+__device__ __forceinline__ void twiddle_all(float2 *v, const float2 *__restrict__ tw, int e, bool inv) {
+    using fftdev::cmul;
+    if constexpr (R == 16 || R == 8) {
+        const float2 w1 = fftdev::twiddle(tw, e, inv), w4 = fftdev::twiddle(tw, 4 * e, inv);
+        const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], cmul(w4, w1));
+        v[6] = cmul(v[6], cmul(w4, w2));
+        v[7] = cmul(v[7], cmul(w4, w3));
+        if constexpr (R == 16) {
+            const float2 w8 = cmul(w4, w4), w12 = cmul(w8, w4);
+            v[8] = cmul(v[8], w8);
+            v[9] = cmul(v[9], cmul(w8, w1));
+            v[10] = cmul(v[10], cmul(w8, w2));
+            v[11] = cmul(v[11], cmul(w8, w3));
+            v[12] = cmul(v[12], w12);
+            v[13] = cmul(v[13], cmul(w12, w1));
+            v[14] = cmul(v[14], cmul(w12, w2));
+            v[15] = cmul(v[15], cmul(w12, w3));
+        }
+    } else {
+#pragma unroll
+        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], fftdev::twiddle(tw, e * m, inv));
+    }
+}
+
 // Later stage of radix R over span L (constant): in place, or to store() if LAST.
 template <int N, int COUNT, int R, int L, bool LAST, class Store>
 __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
@@ -351,10 +386,7 @@ __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw
         float2 v[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = x[at(pbase, base, m)];
-        if (k > 0) {
-#pragma unroll
-            for (int m = 1; m < R; ++m) v[m] = fftdev::cmul(v[m], fftdev::twiddle(tw, (k * m) << lgtw, inv));
-        }
+        if (k > 0) twiddle_all<R>(v, tw, k << lgtw, inv);
         fftdev::dft<R>(v, inv, tw, N);
         if constexpr (LAST) {
 #pragma unroll
@@ -367,7 +399,48 @@ __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw
     if constexpr (!LAST) __syncthreads();
 }
 
+// First stage for inputs already in the buffer, in natural order at 0..N-1
+// (one transform, at most one butterfly per thread: nthr >= N / R0).  Each
+// thread reads the R0 inputs m (N/R0) + tid, the CTA synchronises, between()
+// runs (the buffer's old contents are dead by then), and the outputs go to
+// their padded digit-reversed slots.
+template <int N, class Between>
+__device__ __forceinline__ void first_inplace(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid,
+                                              Between &between) {
+    using Rd = Radices<N>;
+    using Ly = Layout<N>;
+    constexpr int R = Rd::r0, nb = N / R;
+    const bool active = tid < nb;
+    float2 v[R];
+    if (active) {
+#pragma unroll
+        for (int m = 0; m < R; ++m) v[m] = buf[m * nb + tid];
+    }
+    __syncthreads();
+    between();
+    if (active) {
+        fftdev::dft<R>(v, inv, tw, N);
+        const int d1 = tid >> ilog2(Rd::r2), d2 = tid & (Rd::r2 - 1);
+        float2 *x = buf + Ly::pad((d1 + d2 * Rd::r1) * R);
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = v[m];
+    }
+    __syncthreads();
+}
+
 }  // namespace fftst
+
+// One transform of the compile-time size N whose input sits in buf in natural
+// order (see first_inplace); later stages as in fft_static.
+template <int N, class Between, class Store>
+__device__ __forceinline__ void fft_static_inplace(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid,
+                                                   int nthr, Between between, Store store) {
+    using Rd = fftst::Radices<N>;
+    static_assert(Rd::n == 3, "three-stage plans only");
+    fftst::first_inplace<N>(buf, tw, inv, tid, between);
+    fftst::later<N, 1, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store);
+    fftst::later<N, 1, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store);
+}
 
 // COUNT transforms of the compile-time size N (see fft_many for the contract).
 template <int N, int COUNT, class Load, class Store>

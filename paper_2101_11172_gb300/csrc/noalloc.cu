@@ -106,6 +106,7 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
     // a view of the plan whose workspace pointers are the scratch (scalars and pointers only)
     ws_plan_s v;
     v.dev = p->dev;
+    v.sms = p->sms;
     v.flags = p->flags;
     v.L = p->L;
     v.wdeg = p->wdeg;

@@ -374,6 +374,7 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
         return st;
     }
     p->dev = dev;
+    if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || p->sms < 1) p->sms = 1;
     const size_t plane_bytes = (size_t)Np * Np * sizeof(float2);
     // planes per chunk: all planes if they fit the budget, else a multiple of TT
     size_t free_b = 0, total_b = 0;

@@ -32,33 +32,56 @@ __device__ __forceinline__ void plane_fft(float2 *buf, const FftPlan &F, const f
 
 // -- degridding --------------------------------------------------------------
 
+// One CTA owns image row ii for a run of planes: the corrected row and its z
+// stay in shared memory, so each plane costs the screen, one FFT and the
+// stores of the strips some footprint reads.
 template <int NP>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kRowThreads, 2)
 fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ img,
-                const float2 *__restrict__ zsplit, const uint8_t *__restrict__ col_occ, int plane0,
+                const float2 *__restrict__ zsplit, const uint8_t *__restrict__ col_occ, int plane0, int planes,
                 float2 *__restrict__ stack) {
     extern __shared__ __align__(16) float2 sbuf[];
     const int Np = L.Np, N = L.N, half = N / 2;
-    const int ii0 = blockIdx.x * kPerCta;
-    const int pl = plane0 + (int)blockIdx.y;                     // blockIdx is unsigned: convert first
-    const float t = (float)(pl + L.t_lo);
-    float2 *plane = stack + (size_t)blockIdx.y * Np * Np;
-    // columns of this plane's t-tile that any footprint touches (the others are never read)
-    uint8_t *occ = reinterpret_cast<uint8_t *>(sbuf + kPerCta * F.stride);
-    for (int i = threadIdx.x; i < L.ntu; i += kThreads) occ[i] = col_occ[(pl / TT) * L.ntu + i];
-    __syncthreads();
-    auto load = [&](int b, int J) -> float2 {
-        if (!in_crop(J, half, Np)) return make_float2(0.f, 0.f);
-        const size_t pix = (size_t)(ii0 + b) * N + grid_to_crop(J, half, Np);
-        const float2 g = __ldg(img + pix);
-        float sn, cs;
-        phase_tz(t, __ldg(zsplit + pix), &sn, &cs);          // times exp(-i phi)
-        return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
-    };
-    auto store = [&](int b, int R, float2 v) {
-        if (occ[R / TU]) __stcs(plane + tiled_index(ii0 + b, R, Np), v);
-    };
-    plane_fft<NP, kPerCta>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
+    float2 *irow = sbuf + F.stride;                              // N (F.stride is even: 16-byte aligned)
+    float2 *zrow = irow + N;                                     // N
+    uint8_t *occ = reinterpret_cast<uint8_t *>(zrow + N);        // ntu: strips of the current t-tile
+    const int ii = blockIdx.x, tid = threadIdx.x;
+    // this CTA's planes: an equal share of the chunk's valid planes
+    const int nvalid = min(planes, L.Nw - plane0);
+    const int per = (nvalid + (int)gridDim.y - 1) / (int)gridDim.y;
+    const int p_begin = (int)blockIdx.y * per, p_end = min(nvalid, p_begin + per);
+    if (p_begin >= p_end) return;
+    const size_t pix0 = (size_t)ii * N;
+    for (int jj = tid; jj < N; jj += kRowThreads) {
+        irow[jj] = img[pix0 + jj];
+        zrow[jj] = zsplit[pix0 + jj];
+    }
+    int occ_tt = -1;
+    for (int p = p_begin; p < p_end; ++p) {
+        const int pl = plane0 + p;
+        const float t = (float)(pl + L.t_lo);
+        float2 *plane = stack + (size_t)p * Np * Np;
+        const int tt = pl / TT;
+        __syncthreads();                     // row and z visible; the previous plane's last stage is done
+        if (tt != occ_tt) {                  // uniform across the CTA
+            for (int i = tid; i < L.ntu; i += kRowThreads) occ[i] = col_occ[tt * L.ntu + i];
+            occ_tt = tt;
+            __syncthreads();
+        }
+        auto load = [&](int, int J) -> float2 {
+            if (!in_crop(J, half, Np)) return make_float2(0.f, 0.f);
+            const int jj = grid_to_crop(J, half, Np);
+            const float2 g = irow[jj];
+            float sn, cs;
+            phase_tz(t, zrow[jj], &sn, &cs);                     // times exp(-i phi)
+            return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+        };
+        // columns of this plane's t-tile that no footprint touches are never read
+        auto store = [&](int, int R, float2 v) {
+            if (occ[R / TU]) __stcs(plane + tiled_index(ii, R, Np), v);
+        };
+        plane_fft<NP, 1>(sbuf, F, tw, false, tid, kRowThreads, load, store);
+    }
 }
 
 template <int NP>
@@ -69,6 +92,7 @@ fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
     const int Np = L.Np, half = L.N / 2;
     const int R0 = blockIdx.x * kPerCta;                  // two of the four columns of a block
     const int tt = (plane0 + (int)blockIdx.y) / TT, tu = R0 / TU;
+    if (plane0 + (int)blockIdx.y >= L.Nw) return;         // padding planes of the last t-tile: never read
     if (!col_occ[tt * L.ntu + tu]) return;                // no visibility reads these columns of this plane
     float2 *blk = stack + (size_t)blockIdx.y * Np * Np + (size_t)(R0 >> 2) * Np * CB + (R0 & 3);
     uint8_t *occ = reinterpret_cast<uint8_t *>(sbuf + kPerCta * F.stride);
@@ -95,6 +119,7 @@ inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
     const int Np = L.Np, half = L.N / 2;
     const int R0 = blockIdx.x * kPerCta;
     const int tt = (plane0 + (int)blockIdx.y) / TT, tu = R0 / TU;
+    if (plane0 + (int)blockIdx.y >= L.Nw) return;         // padding planes of the last t-tile: inv_rows skips them
     if (!col_occ[tt * L.ntu + tu]) return;                // all-zero columns: inv_rows skips them too
     float2 *blk = stack + (size_t)blockIdx.y * Np * Np + (size_t)(R0 >> 2) * Np * CB + (R0 & 3);
     uint8_t *occ = reinterpret_cast<uint8_t *>(sbuf + kPerCta * F.stride);
@@ -111,8 +136,22 @@ inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
     plane_fft<NP, kPerCta>(sbuf, F, tw, true, threadIdx.x, kThreads, load, store);
 }
 
+// Asynchronous 8-byte copy global -> shared; src_bytes = 0 writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src, bool read) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(read ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // One CTA owns image row ii and sums the chunk's planes into a compensated
 // accumulator in shared memory; the last FFT stage screens and accumulates.
+//
+// Compile-time plans double-buffer the row: while plane p is transformed in
+// one buffer, plane p + 1 is copied into the other with cp.async (zeros for
+// strips no footprint touched), so the loads of the next plane overlap the
+// arithmetic of this one.  Each thread copies exactly the elements it reads
+// in the first stage, so its own wait on the copies is enough.
 template <int NP>
 __global__ void __launch_bounds__(kRowThreads, 2)
 inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ stack,
@@ -121,62 +160,138 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 float2 *__restrict__ dirty) {
     extern __shared__ __align__(16) float2 sbuf[];
     const int Np = L.Np, N = L.N, half = N / 2;
-    float2 *zrow = sbuf + F.stride;                              // N (F.stride is even: 16-byte aligned)
-    float4 *srow = reinterpret_cast<float4 *>(zrow + N);         // N: (sum re, sum im, comp re, comp im)
-    uint8_t *occ = reinterpret_cast<uint8_t *>(srow + N);        // ntu: strips of the current t-tile
-    int occ_tt = -1;
     const int ii = blockIdx.x;
     const int tid = threadIdx.x;
     const size_t pix0 = (size_t)ii * N;
-    for (int jj = tid; jj < N; jj += kRowThreads) {
-        zrow[jj] = zsplit[pix0 + jj];
-        srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
-    }
-    __syncthreads();
     const int nvalid = min(planes, L.Nw - plane0);
-    for (int p = 0; p < nvalid; ++p) {
-        const float2 *plane = stack + (size_t)p * Np * Np;
-        const float t = (float)(plane0 + p + L.t_lo);
-        const int tt = (plane0 + p) / TT;
-        if (tt != occ_tt) {                  // uniform across the CTA; the previous plane ended with a barrier
-            for (int i = tid; i < L.ntu; i += kRowThreads) occ[i] = col_occ[tt * L.ntu + i];
-            __syncthreads();
-            occ_tt = tt;
+    if constexpr (NP >= 512) {
+        constexpr int S = fftst::Layout<NP>::stride;             // even: every region stays 16-byte aligned
+        constexpr int R0 = fftst::Radices<NP>::r0, nb = NP / R0;
+        float2 *zrow = sbuf + 2 * S;                             // N
+        float4 *srow = reinterpret_cast<float4 *>(zrow + N);     // N: (sum re, sum im, comp re, comp im)
+        uint32_t mask = 0;                                       // strips of this thread's elements, one t-tile
+        int mask_tt = -1;
+        auto prefetch = [&](int p) {
+            const int tt = (plane0 + p) / TT;
+            float2 *dst = sbuf + (p & 1) * S;
+            const float2 *plane = stack + (size_t)p * Np * Np;
+            if (tid < nb) {
+                if (tt != mask_tt) {
+                    mask = 0;
+#pragma unroll
+                    for (int m = 0; m < R0; ++m) mask |= (uint32_t)(__ldg(col_occ + tt * L.ntu + (m * nb + tid) / TU) != 0) << m;
+                    mask_tt = tt;
+                }
+#pragma unroll
+                for (int m = 0; m < R0; ++m) {
+                    const int R = m * nb + tid;
+                    cp_async8(dst + R, plane + tiled_index(ii, R, Np), (mask >> m) & 1u);
+                }
+            }
+            cp_async_commit();
+        };
+        for (int jj = tid; jj < N; jj += kRowThreads) {
+            zrow[jj] = zsplit[pix0 + jj];
+            srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
         }
-        // column strips no footprint touched were never transformed: they are zero
-        auto load = [&](int, int R) -> float2 {
-            return occ[R / TU] ? __ldcs(plane + tiled_index(ii, R, Np)) : make_float2(0.f, 0.f);
-        };
-        auto store = [&](int, int J, float2 v) {
-            if (!in_crop(J, half, Np)) return;
-            const int jj = grid_to_crop(J, half, Np);
-            float sn, cs;
-            phase_tz(t, zrow[jj], &sn, &cs);
-            float4 a = srow[jj];
-            kahan_add(a.x, a.z, v.x * cs - v.y * sn);
-            kahan_add(a.y, a.w, v.x * sn + v.y * cs);
-            srow[jj] = a;
-        };
-        plane_fft<NP, 1>(sbuf, F, tw, true, tid, kRowThreads, load, store);
+        if (nvalid > 0) prefetch(0);
         __syncthreads();
-    }
-    for (int jj = tid; jj < N; jj += kRowThreads) {
-        const float4 a = srow[jj];
-        if (last) {
-            const float h = corr[pix0 + jj];
-            dirty[pix0 + jj] = make_float2(h * (a.x - a.z), h * (a.y - a.w));
-        } else {
-            acc[pix0 + jj] = a;
+        for (int p = 0; p < nvalid; ++p) {
+            const float t = (float)(plane0 + p + L.t_lo);
+            cp_async_wait_all();
+            auto between = [&]() {
+                if (p + 1 < nvalid) prefetch(p + 1);
+            };
+            auto store = [&](int, int J, float2 v) {
+                if (!in_crop(J, half, Np)) return;
+                const int jj = grid_to_crop(J, half, Np);
+                float sn, cs;
+                phase_tz(t, zrow[jj], &sn, &cs);
+                float4 a = srow[jj];
+                kahan_add(a.x, a.z, v.x * cs - v.y * sn);
+                kahan_add(a.y, a.w, v.x * sn + v.y * cs);
+                srow[jj] = a;
+            };
+            fft_static_inplace<NP>(sbuf + (p & 1) * S, tw, true, tid, kRowThreads, between, store);
+        }
+        __syncthreads();
+        for (int jj = tid; jj < N; jj += kRowThreads) {
+            const float4 a = srow[jj];
+            if (last) {
+                const float h = corr[pix0 + jj];
+                dirty[pix0 + jj] = make_float2(h * (a.x - a.z), h * (a.y - a.w));
+            } else {
+                acc[pix0 + jj] = a;
+            }
+        }
+    } else {
+        float2 *zrow = sbuf + F.stride;                          // N (F.stride is even: 16-byte aligned)
+        float4 *srow = reinterpret_cast<float4 *>(zrow + N);     // N: (sum re, sum im, comp re, comp im)
+        uint8_t *occ = reinterpret_cast<uint8_t *>(srow + N);    // ntu: strips of the current t-tile
+        int occ_tt = -1;
+        for (int jj = tid; jj < N; jj += kRowThreads) {
+            zrow[jj] = zsplit[pix0 + jj];
+            srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
+        }
+        __syncthreads();
+        for (int p = 0; p < nvalid; ++p) {
+            const float2 *plane = stack + (size_t)p * Np * Np;
+            const float t = (float)(plane0 + p + L.t_lo);
+            const int tt = (plane0 + p) / TT;
+            if (tt != occ_tt) {                  // uniform across the CTA; the previous plane ended with a barrier
+                for (int i = tid; i < L.ntu; i += kRowThreads) occ[i] = col_occ[tt * L.ntu + i];
+                __syncthreads();
+                occ_tt = tt;
+            }
+            // column strips no footprint touched were never transformed: they are zero
+            auto load = [&](int, int R) -> float2 {
+                return occ[R / TU] ? __ldcs(plane + tiled_index(ii, R, Np)) : make_float2(0.f, 0.f);
+            };
+            auto store = [&](int, int J, float2 v) {
+                if (!in_crop(J, half, Np)) return;
+                const int jj = grid_to_crop(J, half, Np);
+                float sn, cs;
+                phase_tz(t, zrow[jj], &sn, &cs);
+                float4 a = srow[jj];
+                kahan_add(a.x, a.z, v.x * cs - v.y * sn);
+                kahan_add(a.y, a.w, v.x * sn + v.y * cs);
+                srow[jj] = a;
+            };
+            plane_fft<NP, 1>(sbuf, F, tw, true, tid, kRowThreads, load, store);
+            __syncthreads();
+        }
+        for (int jj = tid; jj < N; jj += kRowThreads) {
+            const float4 a = srow[jj];
+            if (last) {
+                const float h = corr[pix0 + jj];
+                dirty[pix0 + jj] = make_float2(h * (a.x - a.z), h * (a.y - a.w));
+            } else {
+                acc[pix0 + jj] = a;
+            }
         }
     }
 }
 
 // transform buffers + one occupancy byte per strip (at most N'/16 or N'/32 of them)
-
-// transform buffers + one occupancy byte per strip (at most N'/16 or N'/32 of them)
 inline size_t smem2(const FftPlan &F) { return (size_t)kPerCta * F.stride * sizeof(float2) + F.n / TU + 16; }
+inline size_t smem_fwd_rows(const FftPlan &F, int N) {
+    return (size_t)F.stride * sizeof(float2) + (size_t)N * 2 * sizeof(float2) + F.n / TU + 16;
+}
+// CTAs per image row in fwd_rows: enough rows x groups for about eight CTAs per SM
+inline int row_groups(int N, int planes, int sms) {
+    const int want = (8 * sms + N - 1) / N;
+    return want < 1 ? 1 : (want > planes ? (planes > 0 ? planes : 1) : want);
+}
 inline size_t smem_rows(const FftPlan &F, int N) {
     return (size_t)F.stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4)) + F.n / TU + 16;
+}
+// inv_rows: compile-time plans keep two row buffers and no occupancy bytes
+template <int NP>
+inline size_t smem_inv_rows(const FftPlan &F, int N) {
+    if constexpr (NP >= 512)
+        return (size_t)2 * fftst::Layout<NP>::stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4));
+    else
+        return smem_rows(F, N);
 }
 
 template <typename K>
@@ -189,14 +304,15 @@ template <int NP>
 struct Transforms {
     static cudaError_t setup(const FftPlan &F, int N) {
         cudaError_t e;
-        if ((e = allow_smem(fwd_rows_kernel<NP>, smem2(F))) != cudaSuccess) return e;
+        if ((e = allow_smem(fwd_rows_kernel<NP>, smem_fwd_rows(F, N))) != cudaSuccess) return e;
         if ((e = allow_smem(fwd_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
         if ((e = allow_smem(inv_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
-        return allow_smem(inv_rows_kernel<NP>, smem_rows(F, N));
+        return allow_smem(inv_rows_kernel<NP>, smem_inv_rows<NP>(F, N));
     }
     static cudaError_t fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
-        fwd_rows_kernel<NP><<<dim3(p->L.N / kPerCta, planes), kThreads, smem2(p->fft), s>>>(
-            p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit, p->d_col_occ, chunk * p->P, p->d_stack);
+        fwd_rows_kernel<NP><<<dim3(p->L.N, row_groups(p->L.N, planes, p->sms)), kRowThreads, smem_fwd_rows(p->fft, p->L.N),
+                              s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit, p->d_col_occ, chunk * p->P, planes,
+                                   p->d_stack);
         return cudaGetLastError();
     }
     static cudaError_t fwd_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
@@ -211,7 +327,7 @@ struct Transforms {
     }
     static cudaError_t inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
                                 cudaStream_t s) {
-        inv_rows_kernel<NP><<<p->L.N, kRowThreads, smem_rows(p->fft, p->L.N), s>>>(
+        inv_rows_kernel<NP><<<p->L.N, kRowThreads, smem_inv_rows<NP>(p->fft, p->L.N), s>>>(
             p->L, p->fft, p->d_tw, p->d_stack, p->d_col_occ, chunk * p->P, planes, p->d_zsplit, p->d_corr,
             p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty);
         return cudaGetLastError();

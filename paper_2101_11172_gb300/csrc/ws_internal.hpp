@@ -49,6 +49,7 @@ struct Launch {            // geometry the kernels need
 
 struct ws_plan_s {
     int dev = -1;
+    int sms = 1;                   // multiprocessors of dev (grid sizing)
     uint32_t flags = 0;
     ws::Launch L{};
     double x0 = 0.0, fov = 0.0, w_min = 0.0, w_max = 0.0;
