@@ -240,21 +240,41 @@ __global__ void scan_add_kernel(uint32_t *__restrict__ out, const uint32_t *__re
 // pair of its list in shared memory and writes the tile exactly once.
 // ---------------------------------------------------------------------------
 constexpr int kGridThreads = 256;
-constexpr int kTileCells = TT * TV * TU;
+constexpr int kRowPad = TU + 1;                 // shared row stride: rows b and b + 2 fall in different banks
+constexpr int kTileSlots = TT * TV * kRowPad;
 
-__global__ void __launch_bounds__(kGridThreads)
+// Taps [a0, a1) of a footprint that land in a tile, at tile-local index a - off.
+struct Span {
+    int a0, a1, off;
+};
+
+// The footprint covers positions first .. first + W - 1 and the tile org ..
+// org + T - 1 of a periodic axis of length n >= T: the tile starts d = org -
+// first (mod n) past the footprint's start, and if it runs past n it also
+// covers the footprint's first d + T - n positions.  Returns 0, 1 or 2 spans.
+__device__ __forceinline__ int tile_spans(int org, int first, int n, int W, int T, Span &s0, Span &s1) {
+    int d = org - first;
+    if (d < 0) d += n;
+    const Span inside{d, min(W, d + T), d}, wrapped{0, min(W, d + T - n), d - n};
+    const bool has_inside = d < W, has_wrapped = d + T > n;
+    s0 = has_inside ? inside : wrapped;
+    s1 = wrapped;
+    return (int)has_inside + (int)has_wrapped;
+}
+
+__global__ void __launch_bounds__(kGridThreads, 5)
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
               uint32_t tile_base, int chunk_tt0, float2 *__restrict__ stack) {
-    __shared__ float sre[kTileCells];
-    __shared__ float sim[kTileCells];
+    __shared__ float sre[kTileSlots];
+    __shared__ float sim[kTileSlots];
     __shared__ float swt[kGridThreads / 32][3 * kMaxW];
     const uint32_t tile = tile_base + blockIdx.x;
     if (offsets[tile] == offsets[tile + 1]) return;   // empty tile: the transforms treat it as zero
     const int tu = tile % L.ntu;
     const int tv = (tile / L.ntu) % L.ntv;
     const int tt = tile / (L.ntu * L.ntv);
-    for (int i = threadIdx.x; i < kTileCells; i += kGridThreads) {
+    for (int i = threadIdx.x; i < kTileSlots; i += kGridThreads) {
         sre[i] = 0.f;
         sim[i] = 0.f;
     }
@@ -267,20 +287,35 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     for (uint32_t e = beg + warp; e < end; e += kGridThreads / 32) {
         const VisRec r = rec[list[e]];
         warp_weights(coef, deg, W, r, lane, wt);
-        for (int pair = lane; pair < W * W; pair += 32) {
-            const int a = pair % W, b = pair / W;
-            const int lc = wrap_add(r.r0, a, Np) - u_org;
-            const int lr = wrap_add(r.s0, b, Np) - v_org;
-            if (lc < 0 || lc >= TU || lr < 0 || lr >= TV) continue;
-            const float wxy = wt[a] * wt[W + b];
-            const float vr = r.vre * wxy, vi = r.vim * wxy;
-            for (int c = 0; c < W; ++c) {
-                const int pl = r.t0 + c - t_org;
-                if (pl < 0 || pl >= TT) continue;
-                const float wz = wt[2 * W + c];
-                const int idx = (pl * TV + lr) * TU + lc;
-                atomicAdd(&sre[idx], vr * wz);
-                atomicAdd(&sim[idx], vi * wz);
+        // the part of the W x W x W footprint inside this tile: taps along u and v
+        // (one span each, two where the tile wraps past the footprint) and planes
+        // c in [c0, c1) at tile plane c - dt
+        Span su[2], sv[2];
+        const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
+        const int nsv = tile_spans(v_org, r.s0, Np, W, TV, sv[0], sv[1]);
+        const int dt = t_org - r.t0;
+        const int c0 = max(0, dt), c1 = min(W, dt + TT);
+#pragma unroll
+        for (int iu = 0; iu < 2; ++iu) {
+            if (iu >= nsu) break;
+#pragma unroll
+            for (int iv = 0; iv < 2; ++iv) {
+                if (iv >= nsv) break;
+                const int na = su[iu].a1 - su[iu].a0, nab = na * (sv[iv].a1 - sv[iv].a0);
+                const float inv_na = 1.0f / (float)na;
+                for (int q = lane; q < nab; q += 32) {
+                    // q = bb na + aa, q < 144: (q + 1/2) / na is at least 1/24 from an integer
+                    const int bb = __float2int_rz(((float)q + 0.5f) * inv_na), aa = q - bb * na;
+                    const int a = su[iu].a0 + aa, b = sv[iv].a0 + bb;
+                    const float wxy = wt[a] * wt[W + b];
+                    const float vr = r.vre * wxy, vi = r.vim * wxy;
+                    int idx = ((c0 - dt) * TV + (b - sv[iv].off)) * kRowPad + (a - su[iu].off);
+                    for (int c = c0; c < c1; ++c, idx += TV * kRowPad) {
+                        const float wz = wt[2 * W + c];
+                        atomicAdd(&sre[idx], vr * wz);
+                        atomicAdd(&sim[idx], vi * wz);
+                    }
+                }
             }
         }
         __syncwarp();
@@ -290,10 +325,10 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     const int p0 = t_org - chunk_tt0 * TT;
     // pairs of cells, ordered (plane, column block, row, pair) so that each
     // column block's TV rows go out as one contiguous run
-    for (int i = threadIdx.x; i < kTileCells / 2; i += kGridThreads) {
+    for (int i = threadIdx.x; i < kTileSlots / kRowPad * TU / 2; i += kGridThreads) {
         const int pair = i & 1, lr = (i >> 1) % TV, blk = (i / (2 * TV)) % (TU / CB), pl = i / (TU * TV / 2);
         const int lc = blk * CB + 2 * pair;
-        const int cell = (pl * TV + lr) * TU + lc;
+        const int cell = (pl * TV + lr) * kRowPad + lc;
         float4 v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
         float2 *dst = stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np);
         *reinterpret_cast<float4 *>(dst) = v;
