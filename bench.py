@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["survey", "tiny", "profile"], default="survey")
+    ap.add_argument("--workload", choices=["survey", "tiny", "profile", "reduced"], default="survey")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -60,6 +60,8 @@ def load_workload(name: str):
         return synth.tiny("A")
     if name == "profile":
         return synth.survey_slab()
+    if name == "reduced":
+        return synth.reduced_cost()
     return synth.survey()
 
 
@@ -306,8 +308,8 @@ def accuracy_sample(wl, v_gpu, d_gpu, n_vis=256, n_pix=32):
     g = make_geometry(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range)
     rng = np.random.default_rng(1234)
     kv = rng.choice(wl.M, n_vis, replace=False)
-    lmn = dft.pixel_lmn(g)
-    v_ref = dft.dft_degrid(wl.uvw[kv], lmn, wl.image)
+    nz_rows, nz_cols = np.nonzero(wl.image)            # the skies are sparse or compact
+    v_ref = dft.dft_degrid(wl.uvw[kv], dft.pixel_lmn(g, nz_rows, nz_cols), wl.image[nz_rows, nz_cols])
     ev = float(np.linalg.norm(v_gpu[kv] - v_ref) / np.linalg.norm(v_ref))
     rows = rng.integers(0, wl.N, n_pix)
     cols = rng.integers(0, wl.N, n_pix)

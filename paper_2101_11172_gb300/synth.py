@@ -191,3 +191,22 @@ def differentiable(N: int = 1024, n_ant: int = 256, n_times: int = 61, fov: floa
     est[rows, cols] = sky[rows, cols] * r.uniform(0.7, 1.3, rows.size)
     est += point_sky(N, 20, r, 0.05, 0.3).real
     return Chi2Workload(f"chi2-N{N}-M{uvw.shape[0]}", N, x0, W, fov, uvw, sky, noise, sigma=sigma, estimate=est)
+
+
+def reduced_cost(N: int = 4096, n_ant: int = 256, n_times: int = 1532, fov: float = 0.5, W: int = 5,
+                 x0: float = 0.375, sigma: float = 0.01, n_src: int = 500, index: int = 2) -> Workload:
+    """Reduced-cost setting: image 4096 x 4096 from a 5600 x 5600 grid, W = 5.
+
+    The survey array (256 antennas in a 10 km disc, dec -30) tracked for 4 h
+    (hour angles -2 .. +2) with 1532 samples: 32,640 x 1532 = 50,004,480
+    visibilities, max |(u,v)| = 0.45 N / fov.  x0 = 0.375 is the reading of
+    the setting's grid sizes (about 5461 padded, which the 7-smooth rule
+    makes 5600).  Sky: 500 point sources U(0.1, 1) (sparse, so the exact
+    visibilities are cheap); visibilities to grid are CN(0, 1) plus
+    CN(0, sigma^2) noise, stored as complex64.
+    """
+    uvw = array_uvw(n_ant, 10_000.0, -30.0, -30.0, (-2.0, 2.0), n_times, 0.45 * N / fov, rng_for(index, 1))
+    image = point_sky(N, n_src, rng_for(index, 2))
+    M = uvw.shape[0]
+    vis = (complex_normal(M, rng_for(index, 3)) + complex_normal(M, rng_for(index, 4), sigma)).astype(np.complex64)
+    return Workload(f"reduced-cost-N{N}-M{M}", N, x0, W, fov, uvw, image, vis)
