@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["survey", "tiny", "profile", "reduced"], default="survey")
+    ap.add_argument("--workload", choices=["survey", "tiny", "profile", "reduced", "batched"], default="survey")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -297,6 +297,103 @@ def run_reference(args):
     return 0
 
 
+# -- the batched serving workload -----------------------------------------------
+
+def run_batched(args):
+    """64 independent instances (images 512^2 .. 2048^2, 10^4 .. 5x10^6 visibilities):
+    aggregate grid + degrid throughput of one ws_batch call pair against the same
+    instances run one after another through single plans, and sampled errors against
+    the exact DFT per instance."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from oracle import dft
+    from oracle.geometry import make_geometry
+    from paper_2101_11172_gb300 import synth
+    from paper_2101_11172_gb300.batch import Batch
+    from paper_2101_11172_gb300.wstack import Plan
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wls = synth.batched()
+    M_total = sum(w.M for w in wls)
+    uvw = [torch.from_numpy(w.uvw).to(dev) for w in wls]
+    img = [torch.from_numpy(w.image.astype(np.complex64)).to(dev) for w in wls]
+    vis = [torch.from_numpy(w.vis).to(dev) for w in wls]
+    stream = torch.cuda.current_stream(dev)
+    b = Batch([(w.N, w.fov, w.w_range[0], w.w_range[1], w.M) for w in wls], wls[0].x0, wls[0].W, device=dev)
+    vout = [torch.empty(w.M, dtype=torch.complex64, device=dev) for w in wls]
+    dout = [torch.empty(w.N, w.N, dtype=torch.complex64, device=dev) for w in wls]
+
+    def step():
+        b.degrid(img, uvw, out=vout)
+        b.grid(uvw, vis, out=dout)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same instances, one plan at a time (each with its own full w-stack)
+    ms_seq = 0.0
+    for i, w in enumerate(wls):
+        with Plan(w.N, w.x0, w.W, w.fov, *w.w_range, device=dev) as p:
+            p.degrid(img[i], uvw[i], out=vout[i])
+            p.grid(uvw[i], vis[i], out=dout[i])
+            torch.cuda.synchronize(dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            p.degrid(img[i], uvw[i], out=vout[i])
+            p.grid(uvw[i], vis[i], out=dout[i])
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_seq += a0.elapsed_time(a1)
+    step()                                   # the batch's own results for the error check
+    torch.cuda.synchronize(dev)
+    errs = []
+    for i, w in enumerate(wls):
+        g = make_geometry(w.N, w.x0, w.W, w.fov, *w.w_range)
+        rng = np.random.default_rng(4000 + i)
+        k = rng.choice(w.M, size=min(32, w.M), replace=False)
+        rows, cols = np.nonzero(w.image)
+        v_ref = dft.dft_degrid(w.uvw[k], dft.pixel_lmn(g, rows, cols), w.image[rows, cols])
+        pr, pc = rng.integers(0, w.N, 2), rng.integers(0, w.N, 2)
+        d_ref = dft.dft_grid(w.uvw, w.vis, dft.pixel_lmn(g, pr, pc))
+        v_gpu = vout[i].cpu().numpy()[k].astype(np.complex128)
+        d_gpu = dout[i].cpu().numpy()[pr, pc].astype(np.complex128)
+        errs.append((float(np.linalg.norm(v_gpu - v_ref) / np.linalg.norm(v_ref)),
+                     float(np.linalg.norm(d_gpu - d_ref) / np.linalg.norm(d_ref))))
+    errs = np.array(errs)
+    Ns = [w.N for w in wls]
+    line = {"metric": "visibilities/sec grid+degrid, 64-instance batch at W=7,x0=0.25", "value": M_total / (ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32 (FP64 coordinates and phase arguments)", "data": "synthetic",
+            "config": {"workload": "batched-64", "instances": len(wls), "visibilities": M_total,
+                       "images": {str(n): Ns.count(n) for n in sorted(set(Ns))},
+                       "visibility_range": [min(w.M for w in wls), max(w.M for w in wls)],
+                       "branches": b.branches},
+            "sequential": {"value": M_total / (ms_seq / 1e3), "ms_per_step": ms_seq,
+                           "what": "the same 64 instances through single plans, one after another"},
+            "speedup_vs_sequential": ms_seq / ms,
+            "accuracy": {"max_degrid_rel_rms_vs_dft": float(errs[:, 0].max()),
+                         "max_grid_rel_rms_vs_dft": float(errs[:, 1].max()),
+                         "median_degrid": float(np.median(errs[:, 0])), "median_grid": float(np.median(errs[:, 1])),
+                         "sampled": "32 visibilities and 2 pixels per instance"},
+            "clocks": clocks.summary()}
+    b.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # -- our path -----------------------------------------------------------------
 
 def accuracy_sample(wl, v_gpu, d_gpu, n_vis=256, n_pix=32):
@@ -325,6 +422,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import numpy as np
     import torch

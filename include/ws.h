@@ -167,6 +167,67 @@ ws_status ws_plan_stats(ws_plan_t plan, ws_stats_t *stats, int32_t reset);
 /* Release the plan's device memory (waits for its work). */
 ws_status ws_destroy(ws_plan_t plan);
 
+/* ---- Batches of independent problems -----------------------------------
+ * Many observations or channels at once, each with its own image size,
+ * field, w-range and visibility count (x0, W and flags shared).  The paper
+ * has no counterpart; this is the serving form of Algorithms 5 and 6.  The
+ * batch builds one plan per instance, exactly as ws_plan would, but no
+ * per-plan w-stack: it deals the instances to `branches` parallel branches
+ * (largest first, each to the least-loaded branch) and gives each branch one
+ * slice of a shared workspace, used by its instances in turn.  A call runs
+ * every instance's kernels, each branch on its own stream, captured once into
+ * a CUDA graph; later calls with the same data pointers replay that graph,
+ * calls with other pointers capture a new one.  Results are those of
+ * ws_grid / ws_degrid on each instance alone.
+ *
+ * Pointer arguments are HOST arrays of n DEVICE pointers (instance order);
+ * each instance's buffers follow the ws_grid / ws_degrid layouts.  The batch
+ * must not be used by two calls at once; buffers must stay valid while a
+ * replayed graph may use them. */
+typedef struct ws_batch_s *ws_batch_t;
+
+typedef struct {
+    int32_t N;             /* image side (as for ws_plan) */
+    double fov;            /* field of view (as for ws_plan) */
+    double w_min, w_max;   /* w-range (as for ws_plan) */
+    int64_t M;             /* visibilities of this instance (fixed for the batch's life) */
+} ws_instance_t;
+
+/* Build a batch of n >= 1 instances.
+ *   x0, W            as for ws_plan, shared by all instances
+ *   branches         1..8 parallel branches, or 0: the first call times the
+ *                    call with 1, 2 and 4 branches and keeps the fastest
+ *   workspace_bytes  device bytes shared by the branches' w-stacks; 0 = the
+ *                    smaller of 60% of free memory and what `branches` (or 4)
+ *                    whole stacks of the largest instance need.  Each slice
+ *                    must hold 8 planes of its largest instance (WS_ERR_OOM)
+ *   flags            WS_FLAG_ASYNC, WS_FLAG_NO_Z_OFFSET
+ * Per-instance parameter errors return WS_ERR_ARG naming the instance. */
+ws_status ws_batch_create(ws_batch_t *out, int32_t n, const ws_instance_t *inst, double x0, int32_t W,
+                          int32_t branches, int64_t workspace_bytes, uint32_t flags);
+
+/* Algorithm 5 on every instance: uvw[i] (device double M_i x 3), vis[i]
+ * (device complex64 M_i) -> dirty[i] (device complex64 N_i x N_i).  Unless
+ * WS_FLAG_ASYNC, waits for the stream and returns WS_ERR_UV_RANGE /
+ * WS_ERR_W_RANGE naming the first instance that dropped visibilities. */
+ws_status ws_batch_grid(ws_batch_t batch, const double *const *uvw, const void *const *vis,
+                        void *const *dirty, ws_stream_t stream);
+
+/* Algorithm 6 on every instance: image[i] (device complex64 N_i x N_i),
+ * uvw[i] -> vis[i] (device complex64 M_i, overwritten). */
+ws_status ws_batch_degrid(ws_batch_t batch, const void *const *image, const double *const *uvw,
+                          void *const *vis, ws_stream_t stream);
+
+/* Plan parameters of instance i and the branch it runs on (-1 before the
+ * branch count is chosen); branch may be NULL. */
+ws_status ws_batch_info(ws_batch_t batch, int32_t i, ws_plan_info_t *info, int32_t *branch);
+
+/* Branch count in use (0 until the first call of a batch made with branches = 0). */
+ws_status ws_batch_branches(ws_batch_t batch, int32_t *branches);
+
+/* Release the batch's plans, workspace, streams and graphs (waits for its work). */
+ws_status ws_batch_destroy(ws_batch_t batch);
+
 /* Message for the calling thread's latest non-WS_OK status ("" if none). */
 const char *ws_last_error(void);
 

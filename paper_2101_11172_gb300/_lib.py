@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_ARG", 2: "WS_ERR_UV_RANGE", 3: "WS_ERR_W_
 
 # every entry point declared in include/ws.h
 EXPORTS = ("ws_plan", "ws_degrid", "ws_grid", "ws_degrid_noalloc", "ws_plan_dropped", "ws_plan_info",
-           "ws_plan_stats", "ws_destroy", "ws_last_error")
+           "ws_plan_stats", "ws_destroy", "ws_batch_create", "ws_batch_grid", "ws_batch_degrid",
+           "ws_batch_info", "ws_batch_branches", "ws_batch_destroy", "ws_last_error")
 
 
 class PlanInfo(ctypes.Structure):
@@ -41,6 +42,12 @@ class Stats(ctypes.Structure):
         return {"calls": self.calls, "kernel_launches": self.kernel_launches,
                 "stage_ms": {n: self.stage_ms[i] for i, n in enumerate(STAGES)},
                 "stage_launches": {n: self.stage_launches[i] for i, n in enumerate(STAGES)}}
+
+
+class Instance(ctypes.Structure):
+    """ws_instance_t: one problem of a batch."""
+    _fields_ = [("N", ctypes.c_int32), ("fov", ctypes.c_double), ("w_min", ctypes.c_double),
+                ("w_max", ctypes.c_double), ("M", ctypes.c_int64)]
 
 
 class WsError(RuntimeError):
@@ -69,6 +76,13 @@ def load(path: str = LIB) -> ctypes.CDLL:
     lib.ws_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
     lib.ws_plan_stats.argtypes = [vp, ctypes.POINTER(Stats), i32]
     lib.ws_destroy.argtypes = [vp]
+    pp = ctypes.POINTER(vp)
+    lib.ws_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Instance), dbl, i32, i32, i64, u32]
+    lib.ws_batch_grid.argtypes = [vp, pp, pp, pp, vp]
+    lib.ws_batch_degrid.argtypes = [vp, pp, pp, pp, vp]
+    lib.ws_batch_info.argtypes = [vp, i32, ctypes.POINTER(PlanInfo), ctypes.POINTER(i32)]
+    lib.ws_batch_branches.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.ws_batch_destroy.argtypes = [vp]
     lib.ws_last_error.argtypes = []
     lib.ws_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -134,6 +148,51 @@ def ws_plan_stats(plan: int, reset: bool = False) -> Stats:
 
 def ws_destroy(plan: int) -> None:
     _check(load().ws_destroy(plan))
+
+
+def _ptrs(values):
+    arr = (ctypes.c_void_p * len(values))(*[int(v) for v in values])
+    return arr
+
+
+def ws_batch_create(instances, x0: float, W: int, branches: int = 0, workspace_bytes: int = 0,
+                    flags: int = 0) -> int:
+    """instances: sequence of (N, fov, w_min, w_max, M)."""
+    arr = (Instance * len(instances))(*[Instance(int(N), float(fov), float(a), float(b), int(M))
+                                        for (N, fov, a, b, M) in instances])
+    h = ctypes.c_void_p()
+    _check(load().ws_batch_create(ctypes.byref(h), len(instances), arr, x0, W, branches, workspace_bytes, flags))
+    return h.value
+
+
+def ws_batch_grid(batch: int, uvw_ptrs, vis_ptrs, dirty_ptrs, stream: int = 0) -> int:
+    st = load().ws_batch_grid(batch, _ptrs(uvw_ptrs), _ptrs(vis_ptrs), _ptrs(dirty_ptrs), stream)
+    if st not in (WS_OK, WS_ERR_UV_RANGE, WS_ERR_W_RANGE):
+        _check(st)
+    return st
+
+
+def ws_batch_degrid(batch: int, image_ptrs, uvw_ptrs, vis_ptrs, stream: int = 0) -> int:
+    st = load().ws_batch_degrid(batch, _ptrs(image_ptrs), _ptrs(uvw_ptrs), _ptrs(vis_ptrs), stream)
+    if st not in (WS_OK, WS_ERR_UV_RANGE, WS_ERR_W_RANGE):
+        _check(st)
+    return st
+
+
+def ws_batch_info(batch: int, i: int):
+    info, branch = PlanInfo(), ctypes.c_int32()
+    _check(load().ws_batch_info(batch, i, ctypes.byref(info), ctypes.byref(branch)))
+    return info, branch.value
+
+
+def ws_batch_branches(batch: int) -> int:
+    k = ctypes.c_int32()
+    _check(load().ws_batch_branches(batch, ctypes.byref(k)))
+    return k.value
+
+
+def ws_batch_destroy(batch: int) -> None:
+    _check(load().ws_batch_destroy(batch))
 
 
 def ws_last_error() -> str:

@@ -92,30 +92,6 @@ void release(ws_plan_s *p) {
     delete p;
 }
 
-// Grow the per-call buffers to hold M visibilities.
-ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid) {
-    if (M > p->rec_cap) {
-        cudaFree(p->d_rec);
-        p->bytes -= p->rec_cap * (int64_t)sizeof(ws::VisRec);
-        p->rec_cap = 0;
-        cudaError_t e = dev_alloc(&p->d_rec, (size_t)M, &p->bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "allocating visibility records");
-        p->rec_cap = M;
-    }
-    // gridding: at most (2 x 2 x ceil((W-1)/TT + 1)) tiles per visibility
-    const int64_t per = grid ? 4 * ((p->L.W - 1 + TT - 1) / TT + 1) : 1;
-    const int64_t need = M * per;
-    if (need > p->list_cap) {
-        cudaFree(p->d_list);
-        p->bytes -= p->list_cap * 4;
-        p->list_cap = 0;
-        cudaError_t e = dev_alloc(&p->d_list, (size_t)need, &p->bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "allocating tile lists");
-        p->list_cap = need;
-    }
-    return WS_OK;
-}
-
 cudaEvent_t take_event(ws_plan_s *p) {
     if (!p->free_events.empty()) {
         cudaEvent_t e = p->free_events.back();
@@ -237,6 +213,31 @@ ws_status finish_call(ws_plan_s *p, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Grow the per-call buffers to hold M visibilities.
+ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid) {
+    if (M > p->rec_cap) {
+        cudaFree(p->d_rec);
+        p->bytes -= p->rec_cap * (int64_t)sizeof(ws::VisRec);
+        p->rec_cap = 0;
+        cudaError_t e = dev_alloc(&p->d_rec, (size_t)M, &p->bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "allocating visibility records");
+        p->rec_cap = M;
+    }
+    // gridding: at most (2 x 2 x ceil((W-1)/TT + 1)) tiles per visibility
+    const int64_t per = grid ? 4 * ((p->L.W - 1 + TT - 1) / TT + 1) : 1;
+    const int64_t need = M * per;
+    if (need > p->list_cap) {
+        cudaFree(p->d_list);
+        p->bytes -= p->list_cap * 4;
+        p->list_cap = 0;
+        cudaError_t e = dev_alloc(&p->d_list, (size_t)need, &p->bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "allocating tile lists");
+        p->list_cap = need;
+    }
+    return WS_OK;
+}
+
 }  // namespace ws
 
 using namespace ws;
@@ -247,6 +248,15 @@ const char *ws_last_error(void) { return g_last_error.c_str(); }
 
 ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
                   uint32_t flags) {
+    return ws::plan_create(out, N, x0, W, fov, w_min, w_max, flags, true);
+}
+
+}  // extern "C"
+
+namespace ws {
+
+ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
+                      uint32_t flags, bool own_stack) {
     if (!out) {
         set_error("ws_plan: out is NULL");
         return WS_ERR_ARG;
@@ -388,7 +398,7 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
     }
     const int fit_planes = (int)std::min<size_t>(budget / plane_bytes, (size_t)1 << 20);
     if (fit_planes < P) P = std::max(TT, (fit_planes / TT) * TT);
-    p->P = P;
+    p->P = own_stack ? P : 0;             // a batch hands the plan a shared stack later
 
     ws_status st = WS_OK;
     const char *what = nullptr;
@@ -409,7 +419,7 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
     WS_TRY(dev_alloc(&p->d_zsplit, zs.size(), &p->bytes), "allocating z table");
     WS_TRY(cudaMemcpy(p->d_zsplit, zs.data(), zs.size() * sizeof(float2), cudaMemcpyHostToDevice),
            "uploading z table");
-    WS_TRY(dev_alloc(&p->d_stack, (size_t)P * Np * Np, &p->bytes), "allocating the w-stack chunk");
+    if (own_stack) WS_TRY(dev_alloc(&p->d_stack, (size_t)P * Np * Np, &p->bytes), "allocating the w-stack chunk");
     {
         std::vector<float2> tw((size_t)Np);
         for (int64_t m = 0; m < Np; ++m) {
@@ -440,28 +450,14 @@ fail:
     return st;
 }
 
-ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M, void *dirty,
-                  ws_stream_t stream) {
-    if (!plan || M < 0 || !dirty || (M > 0 && (!uvw || !vis)) || M > ((int64_t)1 << 31) / 12) {
-        set_error("ws_grid: invalid argument");
-        return WS_ERR_ARG;
-    }
-    ws_plan_s *p = plan;
-    DeviceScope scope(p->dev);
-    if (!scope.ok) {
-        set_error("ws_grid: cannot select the plan's device");
-        return WS_ERR_CUDA;
-    }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), true);
-    if (st != WS_OK) return st;
+ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, float2 *dirty,
+                       cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(p->d_drop, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "ws_grid: clearing counters");
     p->stats.calls += 1;
     {
         StageTimer t(p, s, WS_STAGE_PREP, M > 0 ? 1 : 0);
-        if ((e = launch_prep(p, uvw, static_cast<const float2 *>(vis), M, true, s)) != cudaSuccess)
-            return cuda_fail(e, "ws_grid: prep kernel");
+        if ((e = launch_prep(p, uvw, vis, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: prep kernel");
     }
     {
         StageTimer t(p, s, WS_STAGE_BIN, M > 0 ? 6 : 3);
@@ -484,32 +480,18 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
         }
         {
             StageTimer t(p, s, WS_STAGE_ROWS_INV, 1);
-            if ((e = launch_inv_rows(p, c, planes, c == 0, c == nchunks - 1, static_cast<float2 *>(dirty), s)) !=
-                cudaSuccess)
+            if ((e = launch_inv_rows(p, c, planes, c == 0, c == nchunks - 1, dirty, s)) != cudaSuccess)
                 return cuda_fail(e, "ws_grid: inv_rows kernel");
         }
     }
-    return finish_call(p, s);
+    return WS_OK;
 }
 
-ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_t M, void *vis,
-                    ws_stream_t stream) {
-    if (!plan || M < 0 || !image || (M > 0 && (!uvw || !vis)) || M > ((int64_t)1 << 31) / 12) {
-        set_error("ws_degrid: invalid argument");
-        return WS_ERR_ARG;
-    }
-    ws_plan_s *p = plan;
-    DeviceScope scope(p->dev);
-    if (!scope.ok) {
-        set_error("ws_degrid: cannot select the plan's device");
-        return WS_ERR_CUDA;
-    }
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), false);
-    if (st != WS_OK) return st;
+ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, int64_t M, float2 *vis,
+                         cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(p->d_drop, 0, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "ws_degrid: clearing counters");
-    if (M == 0) return finish_call(p, s);
+    if (M == 0) return WS_OK;
     if ((e = cudaMemsetAsync(vis, 0, (size_t)M * sizeof(float2), s)) != cudaSuccess)
         return cuda_fail(e, "ws_degrid: clearing the output");
     p->stats.calls += 1;
@@ -525,7 +507,7 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
     }
     {
         StageTimer t(p, s, WS_STAGE_CORRECT, 1);
-        if ((e = launch_correct_image(p, static_cast<const float2 *>(image), s)) != cudaSuccess)
+        if ((e = launch_correct_image(p, image, s)) != cudaSuccess)
             return cuda_fail(e, "ws_degrid: correction kernel");
     }
     const int total = p->L.ntt * TT;
@@ -544,10 +526,54 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
         }
         {
             StageTimer t(p, s, WS_STAGE_DEGRID3D, 1);
-            if ((e = launch_degrid_chunk(p, c, planes, M, static_cast<float2 *>(vis), s)) != cudaSuccess)
+            if ((e = launch_degrid_chunk(p, c, planes, M, vis, s)) != cudaSuccess)
                 return cuda_fail(e, "ws_degrid: degrid3d kernel");
         }
     }
+    return WS_OK;
+}
+
+}  // namespace ws
+
+extern "C" {
+
+ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M, void *dirty,
+                  ws_stream_t stream) {
+    if (!plan || M < 0 || !dirty || (M > 0 && (!uvw || !vis)) || M > kMaxVis) {
+        set_error("ws_grid: invalid argument");
+        return WS_ERR_ARG;
+    }
+    ws_plan_s *p = plan;
+    DeviceScope scope(p->dev);
+    if (!scope.ok) {
+        set_error("ws_grid: cannot select the plan's device");
+        return WS_ERR_CUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), true);
+    if (st != WS_OK) return st;
+    st = enqueue_grid(p, uvw, static_cast<const float2 *>(vis), M, static_cast<float2 *>(dirty), s);
+    if (st != WS_OK) return st;
+    return finish_call(p, s);
+}
+
+ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_t M, void *vis,
+                    ws_stream_t stream) {
+    if (!plan || M < 0 || !image || (M > 0 && (!uvw || !vis)) || M > kMaxVis) {
+        set_error("ws_degrid: invalid argument");
+        return WS_ERR_ARG;
+    }
+    ws_plan_s *p = plan;
+    DeviceScope scope(p->dev);
+    if (!scope.ok) {
+        set_error("ws_degrid: cannot select the plan's device");
+        return WS_ERR_CUDA;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), false);
+    if (st != WS_OK) return st;
+    st = enqueue_degrid(p, static_cast<const float2 *>(image), uvw, M, static_cast<float2 *>(vis), s);
+    if (st != WS_OK) return st;
     return finish_call(p, s);
 }
 

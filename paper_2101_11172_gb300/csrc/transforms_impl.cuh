@@ -294,9 +294,17 @@ inline size_t smem_inv_rows(const FftPlan &F, int N) {
         return smem_rows(F, N);
 }
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
+// (after checking that this plan's need fits): kernels are shared by every
+// plan, so a limit set to one plan's need could be too low for another's.
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (bytes > (size_t)optin) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 // Launchers of one FFT variant.

@@ -99,6 +99,19 @@ namespace ws {
 void set_error(const std::string &msg);
 ws_status cuda_fail(cudaError_t e, const char *what);
 
+// Tile lists are indexed with 32-bit offsets and hold at most 12 entries per visibility.
+constexpr int64_t kMaxVis = ((int64_t)1 << 31) / 12;
+
+// Plan construction and the enqueue-only halves of ws_grid / ws_degrid (plan.cpp).
+// own_stack = false leaves d_stack unset and P = 0 for a batch to assign.
+ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
+                      uint32_t flags, bool own_stack);
+ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid);
+ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, float2 *dirty,
+                       cudaStream_t s);
+ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, int64_t M, float2 *vis,
+                         cudaStream_t s);
+
 // Launchers (wstack.cu).
 cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,
                         bool grid, cudaStream_t s);

@@ -210,3 +210,36 @@ def reduced_cost(N: int = 4096, n_ant: int = 256, n_times: int = 1532, fov: floa
     M = uvw.shape[0]
     vis = (complex_normal(M, rng_for(index, 3)) + complex_normal(M, rng_for(index, 4), sigma)).astype(np.complex64)
     return Workload(f"reduced-cost-N{N}-M{M}", N, x0, W, fov, uvw, image, vis)
+
+
+def batched(n: int = 64, sizes=(512, 1024, 2048), m_range=(1e4, 5e6), W: int = 7, x0: float = 0.25,
+            index: int = 4) -> list:
+    """Serving-style batch: n independent instances, each with its own seeded array and sky.
+
+    Instance i draws from sub-stream 100 + i: image side uniform over
+    ``sizes``; a target visibility count log-uniform in ``m_range``; an
+    array of n_ant antennas (at most what the count allows, at most 256) in
+    a 10 km disc at latitude -30; declination U(-70, 10) degrees; a track of
+    U(1, 8) hours centred on hour angle U(-2, 2); field of view U(0.2, 0.5)
+    rad; max |(u,v)| = 0.45 N / fov; n_src ~ U{20..200} point sources with
+    amplitudes U(0.1, 1); visibilities to grid CN(0, 1) as complex64.
+    M = baselines x times is the target rounded to whole time samples.
+    """
+    out = []
+    for i in range(n):
+        rng = rng_for(index, 100 + i)
+        N = int(rng.choice(sizes))
+        m_target = float(np.exp(rng.uniform(np.log(m_range[0]), np.log(m_range[1]))))
+        ant_max = int((1 + math.sqrt(1 + 8 * m_target)) / 2)
+        n_ant = int(rng.integers(min(16, ant_max), min(256, ant_max) + 1))
+        nbl = n_ant * (n_ant - 1) // 2
+        n_times = max(1, int(round(m_target / nbl)))
+        dec = float(rng.uniform(-70.0, 10.0))
+        span, centre = float(rng.uniform(1.0, 8.0)), float(rng.uniform(-2.0, 2.0))
+        fov = float(rng.uniform(0.2, 0.5))
+        uvw = array_uvw(n_ant, 10_000.0, -30.0, dec, (centre - span / 2, centre + span / 2), n_times,
+                        0.45 * N / fov, rng)
+        image = point_sky(N, int(rng.integers(20, 201)), rng)
+        vis = complex_normal(uvw.shape[0], rng).astype(np.complex64)
+        out.append(Workload(f"batch{i}-N{N}-M{uvw.shape[0]}", N, x0, W, fov, uvw, image, vis))
+    return out

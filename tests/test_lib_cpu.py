@@ -68,3 +68,22 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_batch_argument_validation_needs_no_device(lib):
+    h = ctypes.c_void_p()
+    one = (_lib.Instance * 1)(_lib.Instance(64, 0.2, -1.0, 1.0, 100))
+    # no instances, too many branches, negative workspace, flags a batch does not take
+    assert lib.ws_batch_create(ctypes.byref(h), 0, one, 0.25, 7, 0, 0, 0) == _lib.WS_ERR_ARG
+    assert lib.ws_batch_create(ctypes.byref(h), 1, one, 0.25, 7, 9, 0, 0) == _lib.WS_ERR_ARG
+    assert lib.ws_batch_create(ctypes.byref(h), 1, one, 0.25, 7, 0, -1, 0) == _lib.WS_ERR_ARG
+    assert lib.ws_batch_create(ctypes.byref(h), 1, one, 0.25, 7, 0, 0, _lib.WS_FLAG_TIMING) == _lib.WS_ERR_ARG
+    assert lib.ws_batch_create(None, 1, one, 0.25, 7, 0, 0, 0) == _lib.WS_ERR_ARG
+    neg = (_lib.Instance * 1)(_lib.Instance(64, 0.2, -1.0, 1.0, -5))
+    assert lib.ws_batch_create(ctypes.byref(h), 1, neg, 0.25, 7, 0, 0, 0) == _lib.WS_ERR_ARG
+    assert "instance 0" in _lib.ws_last_error()
+    assert h.value is None
+    assert lib.ws_batch_grid(None, None, None, None, None) == _lib.WS_ERR_ARG
+    assert lib.ws_batch_degrid(None, None, None, None, None) == _lib.WS_ERR_ARG
+    assert lib.ws_batch_info(None, 0, None, None) == _lib.WS_ERR_ARG
+    assert lib.ws_batch_destroy(None) == _lib.WS_OK
