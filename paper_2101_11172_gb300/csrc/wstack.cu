@@ -262,6 +262,11 @@ __device__ __forceinline__ int tile_spans(int org, int first, int n, int W, int 
     return (int)has_inside + (int)has_wrapped;
 }
 
+// Shared-memory FP32 add with no returned value.
+__device__ __forceinline__ void red_add_shared(float *addr, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(addr)), "f"(v) : "memory");
+}
+
 __global__ void __launch_bounds__(kGridThreads, 5)
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
@@ -269,6 +274,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     __shared__ float sre[kTileSlots];
     __shared__ float sim[kTileSlots];
     __shared__ float swt[kGridThreads / 32][3 * kMaxW];
+    __shared__ float scoef[kMaxDeg + 1][32];          // [m][lane]: lane l's polynomial, zero-padded
     const uint32_t tile = tile_base + blockIdx.x;
     if (offsets[tile] == offsets[tile + 1]) return;   // empty tile: the transforms treat it as zero
     const int tu = tile % L.ntu;
@@ -278,15 +284,28 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
         sre[i] = 0.f;
         sim[i] = 0.f;
     }
-    __syncthreads();
     const int W = L.W, Np = L.Np;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // lane l < 3W always evaluates weight (axis l / W, tap l % W)
+    const int w_axis = lane / W;
+    for (int i = threadIdx.x; i < (kMaxDeg + 1) * 32; i += kGridThreads) {
+        const int m = i / 32, l = i % 32, tap = l - (l / W) * W;
+        scoef[m][l] = (l < 3 * W && m <= deg) ? coef[tap * (deg + 1) + m] : 0.f;
+    }
+    __syncthreads();
     const uint32_t beg = offsets[tile], end = offsets[tile + 1];
     const int u_org = tu * TU, v_org = tv * TV, t_org = tt * TT;
     float *wt = swt[warp];
     for (uint32_t e = beg + warp; e < end; e += kGridThreads / 32) {
         const VisRec r = rec[list[e]];
-        warp_weights(coef, deg, W, r, lane, wt);
+        if (lane < 3 * W) {
+            const float nu = w_axis == 0 ? r.nux : (w_axis == 1 ? r.nuy : r.nuz);
+            float acc = scoef[kMaxDeg][lane];
+#pragma unroll
+            for (int m = kMaxDeg - 1; m >= 0; --m) acc = fmaf(acc, nu, scoef[m][lane]);
+            wt[lane] = acc;
+        }
+        __syncwarp();
         // the part of the W x W x W footprint inside this tile: taps along u and v
         // (one span each, two where the tile wraps past the footprint) and planes
         // c in [c0, c1) at tile plane c - dt
@@ -312,8 +331,8 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                     int idx = ((c0 - dt) * TV + (b - sv[iv].off)) * kRowPad + (a - su[iu].off);
                     for (int c = c0; c < c1; ++c, idx += TV * kRowPad) {
                         const float wz = wt[2 * W + c];
-                        atomicAdd(&sre[idx], vr * wz);
-                        atomicAdd(&sim[idx], vi * wz);
+                        red_add_shared(&sre[idx], vr * wz);
+                        red_add_shared(&sim[idx], vi * wz);
                     }
                 }
             }
@@ -346,42 +365,71 @@ __global__ void correct_image_kernel(int64_t n, const float *__restrict__ corr,
 }
 
 // ---------------------------------------------------------------------------
-// Degridding: Algorithm 6 steps 4-5.  One warp per visibility (visiting them
-// in tile order for cache reuse).  Lane <-> (column a, row b) pair of the
-// W x W footprint; each lane walks the footprint's planes, so at every plane
-// the warp reads W contiguous rows of 2-3 column blocks.  Each chunk adds its
-// planes' share to vis, in chunk order.
-// ---------------------------------------------------------------------------
 constexpr int kDegridThreads = 256;
 
+// Degridding: Algorithm 6 steps 4-5.  One warp per visibility (visiting them
+// in tile order for cache reuse); lanes over the W x W (a, b) columns of the
+// footprint (W^2 / 32 rounded up per lane), W planes each.  All of a lane's
+// gathers are issued before any is used, so a warp keeps up to 2 W loads in
+// flight.  The polynomial table sits in shared memory for the weights.  Each
+// chunk adds its planes' share to vis, in chunk order.
+template <int W>
 __global__ void __launch_bounds__(kDegridThreads)
 degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
                 const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_order,
                 const float2 *__restrict__ stack, int plane0, int planes, float2 *__restrict__ vis) {
-    __shared__ float swt[kDegridThreads / 32][3 * kMaxW];
+    constexpr int kPasses = (W * W + 31) / 32;
+    __shared__ float swt[kDegridThreads / 32][3 * W];
+    __shared__ float scoef[W * (kMaxDeg + 1)];
+    for (int i = threadIdx.x; i < W * (deg + 1); i += kDegridThreads) scoef[i] = coef[i];
+    __syncthreads();
     const int64_t widx = ((int64_t)blockIdx.x * kDegridThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (widx >= (int64_t)*n_order) return;      // entries of the sorted list (dropped ones excluded)
     const uint32_t k = order[widx];
     const VisRec r = rec[k];
     if (r.t0 < 0) return;
-    const int W = L.W, Np = L.Np;
+    const int Np = L.Np;
     const int c_lo = max(0, plane0 - r.t0);
     const int c_hi = min(W - 1, plane0 + planes - 1 - r.t0);
     if (c_lo > c_hi) return;
     float *wt = swt[warp];
-    warp_weights(coef, deg, W, r, lane, wt);
-    float ar = 0.f, ai = 0.f;
+    if (lane < 3 * W) {
+        const int axis = lane / W, i = lane - axis * W;
+        const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
+        const float *c = scoef + i * (deg + 1);
+        float acc = c[deg];
+        for (int m = deg - 1; m >= 0; --m) acc = fmaf(acc, nu, c[m]);
+        wt[lane] = acc;
+    }
+    __syncwarp();
     const size_t plane = (size_t)Np * Np;
-    for (int pair = lane; pair < W * W; pair += 32) {
+    const int64_t t_rel = (int64_t)r.t0 - plane0;           // stack plane of tap c is t_rel + c
+    float2 f[kPasses][W];
+#pragma unroll
+    for (int ps = 0; ps < kPasses; ++ps) {
+        const int pair = lane + 32 * ps;
         const int a = pair % W, b = pair / W;
-        const float2 *cell = stack + tiled_index(wrap_add(r.s0, b, Np), wrap_add(r.r0, a, Np), Np);
+        const bool live = pair < W * W;
+        const float2 *cell = stack + tiled_index(wrap_add(r.s0, live ? b : 0, Np), wrap_add(r.r0, a, Np), Np);
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            f[ps][c] = make_float2(0.f, 0.f);
+            if (live && c >= c_lo && c <= c_hi) f[ps][c] = __ldg(cell + (size_t)(t_rel + c) * plane);
+        }
+    }
+    float ar = 0.f, ai = 0.f;
+#pragma unroll
+    for (int ps = 0; ps < kPasses; ++ps) {
+        const int pair = lane + 32 * ps;
+        if (pair >= W * W) break;
+        const int a = pair % W, b = pair / W;
         float sr = 0.f, si = 0.f;
-        for (int c = c_lo; c <= c_hi; ++c) {
-            const float2 f = __ldg(cell + (size_t)(r.t0 + c - plane0) * plane);
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
             const float wc = wt[2 * W + c];
-            sr = fmaf(wc, f.x, sr);
-            si = fmaf(wc, f.y, si);
+            sr = fmaf(wc, f[ps][c].x, sr);
+            si = fmaf(wc, f[ps][c].y, si);
         }
         const float wab = wt[a] * wt[W + b];
         ar = fmaf(wab, sr, ar);
@@ -465,9 +513,30 @@ cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaSt
 cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64_t M, float2 *vis,
                                 cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    degrid3d_kernel<<<blocks_for(M * 32, kDegridThreads), kDegridThreads, 0, s>>>(
-        p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_list, p->d_offsets + p->ntiles, p->d_stack, chunk * p->P,
-        planes, vis);
+    const dim3 grid(blocks_for(M * 32, kDegridThreads));
+#define WS_DEGRID_CASE(w)                                                                                     \
+    case w:                                                                                                  \
+        degrid3d_kernel<w><<<grid, kDegridThreads, 0, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_list,    \
+                                                           p->d_offsets + p->ntiles, p->d_stack,               \
+                                                           chunk * p->P, planes, vis);                         \
+        break;
+    switch (p->L.W) {
+        WS_DEGRID_CASE(1)
+        WS_DEGRID_CASE(2)
+        WS_DEGRID_CASE(3)
+        WS_DEGRID_CASE(4)
+        WS_DEGRID_CASE(5)
+        WS_DEGRID_CASE(6)
+        WS_DEGRID_CASE(7)
+        WS_DEGRID_CASE(8)
+        WS_DEGRID_CASE(9)
+        WS_DEGRID_CASE(10)
+        WS_DEGRID_CASE(11)
+        WS_DEGRID_CASE(12)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef WS_DEGRID_CASE
     return cudaGetLastError();
 }
 
