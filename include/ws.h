@@ -60,7 +60,12 @@ typedef enum {
 enum {
     WS_FLAG_ASYNC = 1u << 0,       /* do not wait for the stream at the end of each call */
     WS_FLAG_NO_Z_OFFSET = 1u << 1, /* Eq. n_params_no_offset: n0 = 1, z in [-z0, 0] */
-    WS_FLAG_TIMING = 1u << 2       /* record CUDA events around every stage (see ws_plan_stats) */
+    WS_FLAG_TIMING = 1u << 2,      /* record CUDA events around every stage (see ws_plan_stats) */
+    WS_FLAG_HERMITIAN = 1u << 3    /* real sky (Section 5.4): a visibility at w < 0 is handled as the
+                                      conjugate visibility at (-u, -v, -w), so only |w| needs planes.
+                                      ws_degrid reads only the real part of the image; ws_grid returns
+                                      the real dirty image Re(sum_k V_k exp(+2 pi i ...)) with a zero
+                                      imaginary part.  The plan's w-range is folded the same way. */
 };
 
 /* Stages of one call, in execution order (Algorithm 5 / Algorithm 6 steps). */
@@ -201,7 +206,7 @@ typedef struct {
  *                    smaller of 60% of free memory and what `branches` (or 4)
  *                    whole stacks of the largest instance need.  Each slice
  *                    must hold 8 planes of its largest instance (WS_ERR_OOM)
- *   flags            WS_FLAG_ASYNC, WS_FLAG_NO_Z_OFFSET
+ *   flags            WS_FLAG_ASYNC, WS_FLAG_NO_Z_OFFSET, WS_FLAG_HERMITIAN
  * Per-instance parameter errors return WS_ERR_ARG naming the instance. */
 ws_status ws_batch_create(ws_batch_t *out, int32_t n, const ws_instance_t *inst, double x0, int32_t W,
                           int32_t branches, int64_t workspace_bytes, uint32_t flags);

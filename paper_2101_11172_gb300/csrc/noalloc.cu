@@ -153,6 +153,8 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
             if ((e = launch_degrid_chunk(&v, c, planes, M, static_cast<float2 *>(vis), s)) != cudaSuccess)
                 return cuda_fail(e, "ws_degrid_noalloc: degrid3d kernel");
         }
+        if (v.L.fold && (e = launch_unfold(&v, uvw, M, static_cast<float2 *>(vis), s)) != cudaSuccess)
+            return cuda_fail(e, "ws_degrid_noalloc: unfolding kernel");
     }
     // the drop counts go to the plan's pinned mirror (allocated by ws_plan)
     if ((e = cudaMemcpyAsync(p->h_drop, drop, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s)) !=

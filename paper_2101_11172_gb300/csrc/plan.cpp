@@ -283,7 +283,7 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         set_error("ws_plan: need finite w_min <= w_max");
         return WS_ERR_ARG;
     }
-    if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_TIMING)) {
+    if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_TIMING | WS_FLAG_HERMITIAN)) {
         set_error("ws_plan: unknown flag bits");
         return WS_ERR_ARG;
     }
@@ -313,6 +313,18 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         nscale = one_minus_nmin / (2.0 * p->x0);
         n0 = 1.0 - p->x0 * nscale;
     }
+    // Section 5.4: with a real sky every w < 0 is folded to -w, so the w-range folds too
+    if (flags & WS_FLAG_HERMITIAN) {
+        const double a = std::fabs(w_min), b = std::fabs(w_max);
+        if (w_min >= 0.0) {
+        } else if (w_max <= 0.0) {
+            w_min = b;
+            w_max = a;
+        } else {
+            w_min = 0.0;
+            w_max = std::max(a, b);
+        }
+    }
     // planes: first tap of w'_min to last tap of w'_max (Section 3.3 tap rule)
     const long long t_lo = (long long)std::floor(nscale * w_min + 0.5 * W) - (W - 1);
     const long long t_hi = (long long)std::floor(nscale * w_max + 0.5 * W);
@@ -333,6 +345,7 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     L.uv_scale = Np * (fov / N);
     L.nscale = nscale;
     L.n0m1 = n0 - 1.0;
+    L.fold = (flags & WS_FLAG_HERMITIAN) ? 1 : 0;
     p->ntiles = (int64_t)L.ntu * L.ntv * L.ntt;
     if (p->ntiles + 1 > (int64_t)4096 * 4096) {
         set_error("ws_plan: too many gridding tiles (N' x N' x planes too large)");
@@ -530,6 +543,8 @@ ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, i
                 return cuda_fail(e, "ws_degrid: degrid3d kernel");
         }
     }
+    if (p->L.fold && (e = launch_unfold(p, uvw, M, vis, s)) != cudaSuccess)
+        return cuda_fail(e, "ws_degrid: unfolding kernel");
     return WS_OK;
 }
 

@@ -219,7 +219,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
             const float4 a = srow[jj];
             if (last) {
                 const float h = corr[pix0 + jj];
-                dirty[pix0 + jj] = make_float2(h * (a.x - a.z), h * (a.y - a.w));
+                dirty[pix0 + jj] = make_float2(h * (a.x - a.z), L.fold ? 0.f : h * (a.y - a.w));
             } else {
                 acc[pix0 + jj] = a;
             }
@@ -264,7 +264,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
             const float4 a = srow[jj];
             if (last) {
                 const float h = corr[pix0 + jj];
-                dirty[pix0 + jj] = make_float2(h * (a.x - a.z), h * (a.y - a.w));
+                dirty[pix0 + jj] = make_float2(h * (a.x - a.z), L.fold ? 0.f : h * (a.y - a.w));
             } else {
                 acc[pix0 + jj] = a;
             }

@@ -43,6 +43,7 @@ struct Launch {            // geometry the kernels need
     int ntu, ntv, ntt;     // tile counts along u, v, t
     double uv_scale;       // u' = u * uv_scale (= N' * dl)
     double nscale, n0m1;   // w' = w * nscale; n0 - 1
+    int fold;              // WS_FLAG_HERMITIAN: w < 0 handled as the conjugate at -(u, v, w)
 };
 
 }  // namespace ws
@@ -119,6 +120,7 @@ cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
 cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s);
 cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s);
+cudaError_t launch_unfold(const ws_plan_s *p, const double *uvw, int64_t M, float2 *vis, cudaStream_t s);
 cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64_t M,
                                 float2 *vis, cudaStream_t s);
 

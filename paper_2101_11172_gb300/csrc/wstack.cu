@@ -50,7 +50,15 @@ __global__ void prep_kernel(Launch L, const double *__restrict__ uvw, const floa
                             unsigned long long *__restrict__ drop) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= M) return;
-    const double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
+    double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
+    // Section 5.4, real sky: V(u, v, w) = conj V(-u, -v, -w), so w < 0 is gridded at
+    // -(u, v, w) with the conjugate value (and degridded there, conjugated afterwards)
+    const bool folded = L.fold && w < 0.0;
+    if (folded) {
+        u = -u;
+        v = -v;
+        w = -w;
+    }
     const int W = L.W;
     VisRec r;
     r.r0 = r.s0 = 0;
@@ -88,7 +96,8 @@ __global__ void prep_kernel(Launch L, const double *__restrict__ uvw, const floa
     float s, c;
     sincospif(2.0f * (float)turns, &s, &c);
     if (grid) {
-        const float2 V = vis[k];
+        float2 V = vis[k];
+        if (folded) V.y = -V.y;
         r.vre = V.x * c - V.y * s;
         r.vim = V.x * s + V.y * c;
     } else {
@@ -355,13 +364,22 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
 }
 
 // Algorithm 6 step 2: image x h_x h_y h_z.
+// A real-sky plan (fold) reads only the real part of the image.
 __global__ void correct_image_kernel(int64_t n, const float *__restrict__ corr,
-                                     const float2 *__restrict__ image, float2 *__restrict__ out) {
+                                     const float2 *__restrict__ image, int fold, float2 *__restrict__ out) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float h = corr[i];
     const float2 f = image[i];
-    out[i] = make_float2(h * f.x, h * f.y);
+    out[i] = make_float2(h * f.x, fold ? 0.f : h * f.y);
+}
+
+// Section 5.4: a visibility with w < 0 was degridded at -(u, v, w); the real
+// sky's visibility at (u, v, w) is the conjugate of that.
+__global__ void unfold_kernel(const double *__restrict__ uvw, int64_t M, float2 *__restrict__ vis) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    if (uvw[3 * k + 2] < 0.0) vis[k].y = -vis[k].y;
 }
 
 // ---------------------------------------------------------------------------
@@ -506,7 +524,14 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
 
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s) {
     const int64_t n = (int64_t)p->L.N * p->L.N;
-    correct_image_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, p->d_corr, image, p->d_img);
+    correct_image_kernel<<<blocks_for(n, 256), 256, 0, s>>>(n, p->d_corr, image, p->L.fold, p->d_img);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unfold(const ws_plan_s *p, const double *uvw, int64_t M, float2 *vis, cudaStream_t s) {
+    (void)p;
+    if (M == 0) return cudaSuccess;
+    unfold_kernel<<<blocks_for(M, 256), 256, 0, s>>>(uvw, M, vis);
     return cudaGetLastError();
 }
 
