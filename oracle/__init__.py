@@ -14,8 +14,11 @@ follows):
   l(x); the top-hat case of Section 6 (W_z = 1, h = 1/sinc).
 * :mod:`oracle.geometry` -- normalised coordinates and plan sizes
   (Section 5.1, Eq. z-on-sphere, Eq. n_params, Eq. N_{w'}+W, Eq. N_w).
-* :mod:`oracle.wstack`   -- Algorithms 1, 2 (1-D) and 5, 6 (3-D improved
-  W-stacking) written step by step in FP64 with numpy's FFT.
+* :mod:`oracle.wstack`   -- Algorithms 1, 2 (1-D), 3, 4 (original W-stacking)
+  and 5, 6 (3-D improved W-stacking) written step by step in FP64 with
+  numpy's FFT.
+* :mod:`oracle.explore`  -- the curves of Figures 3, 5 and 7 (E against W and
+  x0), the top-hat error and the layer counts.
 * :mod:`oracle.dft`      -- the exact operator (Eq. fourier_visibility and its
   adjoint) by brute force, in plain C with a numpy fallback.
 

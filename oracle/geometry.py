@@ -147,3 +147,24 @@ def make_geometry(N: int, x0: float, W: int, fov: float, w_min: float, w_max: fl
     t_hi = int(first_tap(nscale * w_max, W)[0]) + W - 1
     return Geometry(N=N, Np=Np, x0=x0e, W=W, fov=fov, nscale=nscale, n0=n0,
                     t_lo=t_lo, t_hi=t_hi, z_offset=z_offset)
+
+
+def make_geometry_original(N: int, x0: float, W: int, fov: float, w_min: float, w_max: float,
+                           Nw: int) -> Geometry:
+    """Original W-stacking (Algorithms 3 and 4): Nw w-bins of width (w_max - w_min)/Nw.
+
+    The bins are centred on multiples of the bin width (w' = w n_scale with
+    n_scale = Nw / (w_max - w_min) rounded to the nearest integer), a shift of
+    the lattice of Algorithm 3's centres w_min + (t + 1/2) dw that leaves the
+    nearest-bin rule and the spacing unchanged.  The phase of bin t is
+    exp(2 pi i w[t] (n - 1)), so n0 = 1 and z = (n - 1) / n_scale.  W is the
+    width of the two-dimensional (u, v) kernel.
+    """
+    if N <= 0 or N % 2 or Nw < 1 or not w_max > w_min:
+        raise ValueError("need even N > 0, Nw >= 1 and w_max > w_min")
+    Np = fft_size(N, x0)
+    nscale = Nw / (w_max - w_min)
+    t_lo = int(math.floor(nscale * w_min + 0.5))
+    t_hi = int(math.floor(nscale * w_max + 0.5))
+    return Geometry(N=N, Np=Np, x0=N / (2.0 * Np), W=W, fov=fov, nscale=nscale, n0=1.0,
+                    t_lo=t_lo, t_hi=t_hi, z_offset=False)

@@ -156,3 +156,73 @@ def degrid(geom: Geometry, lm: LeastMisfit, image, uvw, with_hz: bool = True):
                 acc += F[rows, (r0[sel] + a) % Np] * (cx[sel, a] * cy[sel, b])
         out[sel] += acc * cz[sel, t - t0[sel]]
     return out * np.conj(prephase(geom, np.asarray(uvw)[:, 2]))  # step 5
+
+
+# -- the original W-stacking: Algorithms 3 and 4 -----------------------------
+
+def _bins(geom: Geometry, uvw):
+    """Nearest bin t = floor(w' + 1/2) of each visibility (Algorithm 3 step 2)."""
+    t = np.floor(np.asarray(uvw, dtype=np.float64)[:, 2] * geom.nscale + 0.5).astype(np.int64)
+    if t.size and (t.min() < geom.t_lo or t.max() > geom.t_hi):
+        raise ValueError("w outside the plan's w-range")
+    return t
+
+
+def grid_original(geom: Geometry, lm: LeastMisfit, uvw, vis):
+    """Algorithm 3: per w-bin 2-D gridding, inverse FFT, crop and exp(2 pi i w[t] (n - 1));
+    the sum over bins times the 2-D gridding correction h_x h_y."""
+    W, Np = geom.W, geom.Np
+    up, vp, _ = geom.scaled(uvw)
+    r0, nux = first_tap(up, W)
+    s0, nuy = first_tap(vp, W)
+    cx, cy = lm.weights(nux), lm.weights(nuy)
+    tb = _bins(geom, uvw)
+    V = np.asarray(vis, dtype=np.complex128)
+    nm1 = geom.pixel_z() * geom.nscale                          # n - 1 on the image
+    idx = _crop_index(geom)
+    acc = np.zeros((geom.N, geom.N), dtype=np.complex128)
+    for t in range(geom.t_lo, geom.t_hi + 1):
+        sel = np.nonzero(tb == t)[0]
+        if not sel.size:
+            continue
+        G = np.zeros((Np, Np), dtype=np.complex128)
+        for b in range(W):                                      # step 3a: 2-D gridding
+            rows = (s0[sel] + b) % Np
+            for a in range(W):
+                np.add.at(G, (rows, (r0[sel] + a) % Np), V[sel] * cy[sel, b] * cx[sel, a])
+        P = np.fft.ifft2(G) * (Np * Np)                         # step 3b
+        turns = (t / geom.nscale) * nm1                         # w[t] (n - 1)
+        acc += P[np.ix_(idx, idx)] * np.exp(2j * np.pi * (turns - np.rint(turns)))  # 3c, 4
+    hx = lm.h(geom.pixel_x())
+    return (hx[None, :] * hx[:, None]) * acc                   # step 5: 2-D correction
+
+
+def degrid_original(geom: Geometry, lm: LeastMisfit, image, uvw):
+    """Algorithm 4: per w-bin correction, exp(-2 pi i w[t] (n - 1)), zero pad, FFT and
+    2-D degridding of the bin's visibilities (the adjoint of grid_original)."""
+    W, Np = geom.W, geom.Np
+    up, vp, _ = geom.scaled(uvw)
+    r0, nux = first_tap(up, W)
+    s0, nuy = first_tap(vp, W)
+    cx, cy = lm.weights(nux), lm.weights(nuy)
+    tb = _bins(geom, uvw)
+    hx = lm.h(geom.pixel_x())
+    corrected = (hx[None, :] * hx[:, None]) * np.asarray(image, dtype=np.complex128)
+    nm1 = geom.pixel_z() * geom.nscale
+    idx = _crop_index(geom)
+    out = np.zeros(r0.shape, dtype=np.complex128)
+    for t in range(geom.t_lo, geom.t_hi + 1):
+        sel = np.nonzero(tb == t)[0]
+        if not sel.size:
+            continue
+        turns = (t / geom.nscale) * nm1
+        Q = np.zeros((Np, Np), dtype=np.complex128)
+        Q[np.ix_(idx, idx)] = corrected * np.exp(-2j * np.pi * (turns - np.rint(turns)))  # step 2a
+        F = np.fft.fft2(Q)                                      # step 2b
+        acc = np.zeros(sel.size, dtype=np.complex128)
+        for b in range(W):                                      # step 2c: 2-D degridding
+            rows = (s0[sel] + b) % Np
+            for a in range(W):
+                acc += F[rows, (r0[sel] + a) % Np] * (cx[sel, a] * cy[sel, b])
+        out[sel] = acc
+    return out
