@@ -513,6 +513,32 @@ def main():
     d2h = M * 8 + wl.N * wl.N * 8
     plan.stats(reset=True)
 
+    # the same step with Section 5.4's folding, when the sky is real (as the survey's is)
+    folded = None
+    if world == 1 and not args.real_sky and not np.any(wl.image.imag):
+        plan_r = Plan(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range, flags=WS_FLAG_HERMITIAN, device=dev)
+
+        def step_r():
+            plan_r.degrid(img, uvw, out=vout)
+            plan_r.grid(uvw, vis, out=dout)
+
+        for _ in range(args.warmup):
+            step_r()
+        torch.cuda.synchronize(dev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            step_r()
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_r = f0.elapsed_time(f1) / args.steps
+        folded = {"value": M / (ms_r / 1e3), "unit": UNIT, "ms_per_step": ms_r, "w_planes": plan_r.Nw,
+                  "what": "WS_FLAG_HERMITIAN: the real sky's w < 0 visibilities folded onto -w (Section 5.4); "
+                          "errors of this mode are in --real-sky runs and tests/test_gpu_parity.py"}
+        plan_r.close()
+        step()                                    # leave vout / dout as the main mode's results
+        torch.cuda.synchronize(dev)
+
     if rank != 0:
         plan.close()
         if world > 1:
@@ -562,6 +588,7 @@ def main():
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
             "gpu_launches": None,
             "roofline": roof, "stages": stages, "accuracy": acc, "clocks": clocks.summary(),
+            "real_sky_folded": folded,
             "cpu_baseline": cpu, "wall_s_timed": t_wall}
     line["gpu_launches"] = int(round(sum(stages[k]["launches_per_step"] for k in ours) * args.steps))
     print(json.dumps(line), flush=True)

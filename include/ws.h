@@ -121,6 +121,21 @@ typedef struct {
 ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov,
                   double w_min, double w_max, uint32_t flags);
 
+/* The original W-stacking (Algorithms 3 and 4), for comparison with the
+ * improved method: Nw w-bins of equal width over [w_min, w_max] (folded first
+ * under WS_FLAG_HERMITIAN), each visibility in its nearest bin, 2-D
+ * least-misfit gridding of width W in u and v, bin phase
+ * exp(2 pi i w[t] (n - 1)) and the 2-D correction h_x h_y only.  Bins are
+ * centred on multiples of the bin width (Algorithm 3 centres them on
+ * w_min + (t + 1/2) dw: the same method on a shifted lattice).  Eq. N_w gives
+ * the customary count Nw >= 2 pi (n_max - n_min)(w_max - w_min); the error
+ * falls only as 1 / Nw (Section 6.2).  W must be odd; plans with fewer than
+ * 2 (n_max - n_min)(w_max - w_min) bins, or with WS_FLAG_NO_Z_OFFSET, return
+ * WS_ERR_ARG.  The plan is used with ws_grid, ws_degrid and the other plan
+ * calls like any other. */
+ws_status ws_plan_original(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov,
+                           double w_min, double w_max, int32_t Nw, uint32_t flags);
+
 /* Algorithm 6: image (device complex64 N x N, read) -> vis (device complex64
  * M, overwritten), for uvw (device double M x 3).  M = 0 is allowed.
  * Visibilities with w outside [w_min, w_max] or non-finite u, v are written as

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_ARG", 2: "WS_ERR_UV_RANGE", 3: "WS_ERR_W_
                 4: "WS_ERR_CUDA", 5: "WS_ERR_OOM", 6: "WS_ERR_TIMEOUT"}
 
 # every entry point declared in include/ws.h
-EXPORTS = ("ws_plan", "ws_degrid", "ws_grid", "ws_degrid_noalloc", "ws_plan_dropped", "ws_plan_info",
+EXPORTS = ("ws_plan", "ws_plan_original", "ws_degrid", "ws_grid", "ws_degrid_noalloc", "ws_plan_dropped", "ws_plan_info",
            "ws_plan_stats", "ws_destroy", "ws_batch_create", "ws_batch_grid", "ws_batch_degrid",
            "ws_batch_info", "ws_batch_branches", "ws_batch_destroy", "ws_last_error")
 
@@ -70,6 +70,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
     lib = ctypes.CDLL(path)
     vp, i32, i64, u32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_double
     lib.ws_plan.argtypes = [ctypes.POINTER(vp), i32, dbl, i32, dbl, dbl, dbl, u32]
+    lib.ws_plan_original.argtypes = [ctypes.POINTER(vp), i32, dbl, i32, dbl, dbl, dbl, i32, u32]
     lib.ws_degrid.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_grid.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_degrid_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
@@ -103,6 +104,13 @@ def _check(status: int):
 def ws_plan(N: int, x0: float, W: int, fov: float, w_min: float, w_max: float, flags: int = 0) -> int:
     h = ctypes.c_void_p()
     _check(load().ws_plan(ctypes.byref(h), N, x0, W, fov, w_min, w_max, flags))
+    return h.value
+
+
+def ws_plan_original(N: int, x0: float, W: int, fov: float, w_min: float, w_max: float, Nw: int,
+                     flags: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().ws_plan_original(ctypes.byref(h), N, x0, W, fov, w_min, w_max, Nw, flags))
     return h.value
 
 

@@ -248,7 +248,22 @@ const char *ws_last_error(void) { return g_last_error.c_str(); }
 
 ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
                   uint32_t flags) {
-    return ws::plan_create(out, N, x0, W, fov, w_min, w_max, flags, true);
+    return ws::plan_create(out, N, x0, W, fov, w_min, w_max, flags, true, 0);
+}
+
+ws_status ws_plan_original(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
+                           int32_t Nw, uint32_t flags) {
+    if (Nw < 1 || W % 2 == 0) {
+        if (out) *out = nullptr;
+        set_error("ws_plan_original: need Nw >= 1 bins and an odd W");
+        return WS_ERR_ARG;
+    }
+    if (flags & WS_FLAG_NO_Z_OFFSET) {
+        if (out) *out = nullptr;
+        set_error("ws_plan_original: the original method has no z offset to remove");
+        return WS_ERR_ARG;
+    }
+    return ws::plan_create(out, N, x0, W, fov, w_min, w_max, flags, true, Nw);
 }
 
 }  // extern "C"
@@ -256,7 +271,7 @@ ws_status ws_plan(ws_plan_t *out, int32_t N, double x0, int32_t W, double fov, d
 namespace ws {
 
 ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
-                      uint32_t flags, bool own_stack) {
+                      uint32_t flags, bool own_stack, int32_t orig_bins) {
     if (!out) {
         set_error("ws_plan: out is NULL");
         return WS_ERR_ARG;
@@ -306,7 +321,34 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     const double r2 = 2.0 * lmax * lmax;
     const double one_minus_nmin = r2 / (1.0 + std::sqrt(1.0 - r2));
     double nscale, n0;
-    if (flags & WS_FLAG_NO_Z_OFFSET) {
+    if (orig_bins > 0) {
+        // Algorithms 3 and 4: orig_bins w-bins over the (folded) w-range, phase
+        // exp(2 pi i w[t] (n - 1)) so n0 = 1; the w-range is folded first
+        double a = w_min, b = w_max;
+        if (flags & WS_FLAG_HERMITIAN) {
+            if (a < 0.0 && b <= 0.0) {
+                const double t = -a;
+                a = -b;
+                b = t;
+            } else if (a < 0.0) {
+                b = std::max(-a, b);
+                a = 0.0;
+            }
+        }
+        if (!(b > a)) {
+            set_error("ws_plan_original: need w_max > w_min");
+            delete p;
+            return WS_ERR_ARG;
+        }
+        nscale = orig_bins / (b - a);
+        n0 = 1.0;
+        // t x z_hi must stay exact in FP32: |z| = |n - 1| / n_scale <= 1/2
+        if (one_minus_nmin / nscale > 0.5) {
+            set_error("ws_plan_original: fewer bins than 2 (n_max - n_min)(w_max - w_min); Eq. N_w asks for pi times more");
+            delete p;
+            return WS_ERR_ARG;
+        }
+    } else if (flags & WS_FLAG_NO_Z_OFFSET) {
         nscale = one_minus_nmin / p->x0;
         n0 = 1.0;
     } else {
@@ -367,7 +409,18 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     }
     std::vector<double> mono;
     monomial_weights(p->fit, 1e-10, kMaxDeg, &p->wdeg, &mono);
+    // two tables of W x (deg + 1): taps along u and v, then taps along w.  The
+    // original method bins in w: only the middle tap (the nearest plane for odd W,
+    // Section 3.3 tap rule) carries weight 1.
     p->wcoef_host.assign(mono.begin(), mono.end());
+    if (orig_bins > 0) {
+        std::vector<float> zt((size_t)W * (p->wdeg + 1), 0.f);
+        zt[(size_t)((W - 1) / 2) * (p->wdeg + 1)] = 1.f;
+        p->wcoef_host.insert(p->wcoef_host.end(), zt.begin(), zt.end());
+    } else {
+        p->wcoef_host.insert(p->wcoef_host.end(), mono.begin(), mono.end());
+    }
+    p->orig_bins = orig_bins;
 
     // correction image h(x_j) h(y_i) h(z_ij) and the split z_ij (Eq. z-on-sphere)
     const double dl = fov / N;
@@ -382,8 +435,12 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
             const double rr = l * l + m * m;
             const double nm1 = -rr / (1.0 + std::sqrt(1.0 - rr));
             double z = (nm1 + (1.0 - n0)) / nscale;
-            z = std::min(std::max(z, -p->x0), p->x0);
-            corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * h_series(p->fit, z));
+            if (orig_bins > 0) {
+                corr[(size_t)i * N + j] = (float)(hx[i] * hx[j]);      // Algorithm 3 step 5: 2-D correction
+            } else {
+                z = std::min(std::max(z, -p->x0), p->x0);
+                corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * h_series(p->fit, z));
+            }
             const double hi = std::nearbyint(z * 8192.0) / 8192.0;
             zs[(size_t)i * N + j] = make_float2((float)hi, (float)(z - hi));
         }

@@ -59,7 +59,8 @@ struct ws_plan_s {
     std::vector<float> wcoef_host;
 
     // device tables (plan lifetime)
-    float *d_wcoef = nullptr;      // W x (wdeg+1)
+    float *d_wcoef = nullptr;      // 2 x W x (wdeg+1): taps along u and v, then along w
+    int orig_bins = 0;             // > 0: original W-stacking with this many w-bins
     float *d_corr = nullptr;       // N x N: h(x_j) h(y_i) h(z_ij)
     float2 *d_zsplit = nullptr;    // N x N: z = hi + lo, hi a multiple of 2^-13
     // stack workspace
@@ -106,7 +107,7 @@ constexpr int64_t kMaxVis = ((int64_t)1 << 31) / 12;
 // Plan construction and the enqueue-only halves of ws_grid / ws_degrid (plan.cpp).
 // own_stack = false leaves d_stack unset and P = 0 for a batch to assign.
 ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
-                      uint32_t flags, bool own_stack);
+                      uint32_t flags, bool own_stack, int32_t orig_bins = 0);
 ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid);
 ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, float2 *dirty,
                        cudaStream_t s);

@@ -22,26 +22,6 @@
 namespace ws {
 namespace {
 
-// c_i(nu) by Horner's rule on the monomial table (FP32).
-__device__ __forceinline__ float tap_weight(const float *__restrict__ coef, int deg, int i, float nu) {
-    const float *c = coef + i * (deg + 1);
-    float acc = __ldg(c + deg);
-    for (int m = deg - 1; m >= 0; --m) acc = fmaf(acc, nu, __ldg(c + m));
-    return acc;
-}
-
-// Lane l < 3W of a warp writes weight (axis l / W, tap l % W) of record r.
-__device__ __forceinline__ void warp_weights(const float *__restrict__ coef, int deg, int W,
-                                             const VisRec &r, int lane, float *swt) {
-    if (lane < 3 * W) {
-        int axis = lane / W;
-        int i = lane - axis * W;
-        float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
-        swt[lane] = tap_weight(coef, deg, i, nu);
-    }
-    __syncwarp();
-}
-
 // ---------------------------------------------------------------------------
 // Pre-processing (Section 3.3 tap rule, Section 5.2 scaling and pre-phase)
 // ---------------------------------------------------------------------------
@@ -283,7 +263,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     __shared__ float sre[kTileSlots];
     __shared__ float sim[kTileSlots];
     __shared__ float swt[kGridThreads / 32][3 * kMaxW];
-    __shared__ float scoef[kMaxDeg + 1][32];          // [m][lane]: lane l's polynomial, zero-padded
+    __shared__ float scoef[kMaxDeg + 1][3 * kMaxW];   // [m][slot]: weight slot l's polynomial, zero-padded
     const uint32_t tile = tile_base + blockIdx.x;
     if (offsets[tile] == offsets[tile + 1]) return;   // empty tile: the transforms treat it as zero
     const int tu = tile % L.ntu;
@@ -295,11 +275,12 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     }
     const int W = L.W, Np = L.Np;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // lane l < 3W always evaluates weight (axis l / W, tap l % W)
-    const int w_axis = lane / W;
-    for (int i = threadIdx.x; i < (kMaxDeg + 1) * 32; i += kGridThreads) {
-        const int m = i / 32, l = i % 32, tap = l - (l / W) * W;
-        scoef[m][l] = (l < 3 * W && m <= deg) ? coef[tap * (deg + 1) + m] : 0.f;
+    // weight slot l < 3W is (axis l / W, tap l % W); lane l evaluates slots l and
+    // l + 32.  coef holds the (u, v) table and then the w table, W x (deg + 1) each.
+    for (int i = threadIdx.x; i < (kMaxDeg + 1) * 3 * kMaxW; i += kGridThreads) {
+        const int m = i / (3 * kMaxW), l = i % (3 * kMaxW), axis = l / W, tap = l - axis * W;
+        const int row = (axis == 2 ? W : 0) + tap;
+        scoef[m][l] = (l < 3 * W && m <= deg) ? coef[row * (deg + 1) + m] : 0.f;
     }
     __syncthreads();
     const uint32_t beg = offsets[tile], end = offsets[tile + 1];
@@ -307,12 +288,13 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     float *wt = swt[warp];
     for (uint32_t e = beg + warp; e < end; e += kGridThreads / 32) {
         const VisRec r = rec[list[e]];
-        if (lane < 3 * W) {
-            const float nu = w_axis == 0 ? r.nux : (w_axis == 1 ? r.nuy : r.nuz);
-            float acc = scoef[kMaxDeg][lane];
+        for (int l = lane; l < 3 * W; l += 32) {
+            const int axis = l / W;
+            const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
+            float acc = scoef[kMaxDeg][l];
 #pragma unroll
-            for (int m = kMaxDeg - 1; m >= 0; --m) acc = fmaf(acc, nu, scoef[m][lane]);
-            wt[lane] = acc;
+            for (int m = kMaxDeg - 1; m >= 0; --m) acc = fmaf(acc, nu, scoef[m][l]);
+            wt[l] = acc;
         }
         __syncwarp();
         // the part of the W x W x W footprint inside this tile: taps along u and v
@@ -398,8 +380,8 @@ degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec 
                 const float2 *__restrict__ stack, int plane0, int planes, float2 *__restrict__ vis) {
     constexpr int kPasses = (W * W + 31) / 32;
     __shared__ float swt[kDegridThreads / 32][3 * W];
-    __shared__ float scoef[W * (kMaxDeg + 1)];
-    for (int i = threadIdx.x; i < W * (deg + 1); i += kDegridThreads) scoef[i] = coef[i];
+    __shared__ float scoef[2 * W * (kMaxDeg + 1)];       // (u, v) table, then the w table
+    for (int i = threadIdx.x; i < 2 * W * (deg + 1); i += kDegridThreads) scoef[i] = coef[i];
     __syncthreads();
     const int64_t widx = ((int64_t)blockIdx.x * kDegridThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -412,13 +394,13 @@ degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec 
     const int c_hi = min(W - 1, plane0 + planes - 1 - r.t0);
     if (c_lo > c_hi) return;
     float *wt = swt[warp];
-    if (lane < 3 * W) {
-        const int axis = lane / W, i = lane - axis * W;
+    for (int l = lane; l < 3 * W; l += 32) {                 // 3W > 32 for W >= 11
+        const int axis = l / W, i = l - axis * W;
         const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
-        const float *c = scoef + i * (deg + 1);
+        const float *c = scoef + ((axis == 2 ? W : 0) + i) * (deg + 1);
         float acc = c[deg];
         for (int m = deg - 1; m >= 0; --m) acc = fmaf(acc, nu, c[m]);
-        wt[lane] = acc;
+        wt[l] = acc;
     }
     __syncwarp();
     const size_t plane = (size_t)Np * Np;

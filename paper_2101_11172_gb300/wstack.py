@@ -16,12 +16,17 @@ class Plan:
     """Improved W-stacking plan (``ws_plan``); see ``include/ws.h``."""
 
     def __init__(self, N: int, x0: float, W: int, fov: float, w_min: float, w_max: float,
-                 flags: int = 0, device=None):
+                 flags: int = 0, device=None, original_bins: int = 0):
+        """``original_bins > 0`` builds the original W-stacking plan (``ws_plan_original``)."""
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
         with torch.cuda.device(self.device):
-            self.handle = _lib.ws_plan(int(N), float(x0), int(W), float(fov), float(w_min),
-                                       float(w_max), int(flags))
+            if original_bins > 0:
+                self.handle = _lib.ws_plan_original(int(N), float(x0), int(W), float(fov), float(w_min),
+                                                    float(w_max), int(original_bins), int(flags))
+            else:
+                self.handle = _lib.ws_plan(int(N), float(x0), int(W), float(fov), float(w_min),
+                                           float(w_max), int(flags))
         info = _lib.ws_plan_info(self.handle)
         self.N, self.Np, self.W, self.Nw = info.N, info.Np, info.W, info.Nw
         self.t_lo, self.planes_per_chunk = info.t_lo, info.planes_per_chunk
