@@ -51,6 +51,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-folded", action="store_true", help="skip the real-sky folded timing")
     ap.add_argument("--real-sky", action="store_true",
                     help="fold w < 0 onto -w (Section 5.4, WS_FLAG_HERMITIAN): real image, real dirty image")
     return ap.parse_args()
@@ -189,18 +190,19 @@ def library_source_sha() -> str:
     return h.hexdigest()
 
 
-def traffic_for(stage: str, planes: int):
-    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
-    scaled to this launch's planes; None if the sources changed since the capture."""
+def traffic_for(stage: str, workload: str, planes: int):
+    """DRAM bytes of one launch of a stage from the committed ncu summary
+    (profiles/traffic.json, one capture of this workload); None if the library
+    sources changed since, or the capture had another workload or plane count."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             data = json.load(f)
-        ent = data.get(stage)
-        if ent and data.get("source_sha256") == library_source_sha() and "planes_profile" in ent \
-                and "dram_bytes_per_launch_full" in ent:
-            return int(ent["dram_bytes_per_launch_profile"] / ent["planes_profile"] * planes)
-    except (OSError, ValueError, KeyError):
+        ent = data.get("stages", {}).get(stage)
+        if ent and data.get("source_sha256") == library_source_sha() and data.get("workload") == workload \
+                and ent.get("planes") == planes:
+            return int(ent["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError, TypeError):
         pass
     return None
 
@@ -515,7 +517,7 @@ def main():
 
     # the same step with Section 5.4's folding, when the sky is real (as the survey's is)
     folded = None
-    if world == 1 and not args.real_sky and not np.any(wl.image.imag):
+    if world == 1 and not args.real_sky and not args.no_folded and not np.any(wl.image.imag):
         plan_r = Plan(wl.N, wl.x0, wl.W, wl.fov, *wl.w_range, flags=WS_FLAG_HERMITIAN, device=dev)
 
         def step_r():
@@ -565,7 +567,7 @@ def main():
     d = stages[dom]
     roof = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
             "frac": None if d["gbs"] is None else d["gbs"] / peak, "peak_source": peak_src,
-            "traffic": traffic_for(dom, total_planes // nchunks)}
+            "traffic": traffic_for(dom, wl.name, total_planes // nchunks)}
     # the CPU baseline leg: the only place this arm runs the oracle (its rate, and
     # the exact DFT on sampled outputs for the error half of the metric)
     cpu, acc = None, {}
