@@ -149,6 +149,40 @@ __device__ __forceinline__ void dft<7>(float2 *v, bool inv, const float2 *__rest
     dft_odd<7>(v, inv, tw, n);
 }
 
+// v[m] *= w^m for m = 1..R-1, w = exp(-+ 2 pi i e / n).  The table holds w^m
+// to half an ulp, but a warp's loads of w^m for m > 1 scatter over many
+// sectors; so only w and w^4 are read and the other powers are products of
+// them (at most five roundings: RMS error about 7e-8 against 2e-8 for the
+// table, far below the FP32 transform's own rounding).
+template <int R>
+__device__ __forceinline__ void twiddle_all(float2 *v, const float2 *__restrict__ tw, int e, bool inv) {
+    if constexpr (R == 16 || R == 8) {
+        const float2 w1 = twiddle(tw, e, inv), w4 = twiddle(tw, 4 * e, inv);
+        const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], cmul(w4, w1));
+        v[6] = cmul(v[6], cmul(w4, w2));
+        v[7] = cmul(v[7], cmul(w4, w3));
+        if constexpr (R == 16) {
+            const float2 w8 = cmul(w4, w4), w12 = cmul(w8, w4);
+            v[8] = cmul(v[8], w8);
+            v[9] = cmul(v[9], cmul(w8, w1));
+            v[10] = cmul(v[10], cmul(w8, w2));
+            v[11] = cmul(v[11], cmul(w8, w3));
+            v[12] = cmul(v[12], w12);
+            v[13] = cmul(v[13], cmul(w12, w1));
+            v[14] = cmul(v[14], cmul(w12, w2));
+            v[15] = cmul(v[15], cmul(w12, w3));
+        }
+    } else {
+#pragma unroll
+        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], twiddle(tw, e * m, inv));
+    }
+}
+
 // In-place decimation-in-time stage of radix R: for every block b of R*L
 // positions and offset k < L, the R elements at b*R*L + k + m*L (m < R) are
 // multiplied by w_{RL}^{k m}, transformed by an R-point DFT and written back
@@ -182,11 +216,7 @@ __device__ __forceinline__ void dit_stage(float2 *buf, const FftPlan &P, int L, 
         float2 v[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = x[fft_pad(base + m * L, P.padshift)];
-        if (k > 0) {
-#pragma unroll
-            for (int m = 1; m < R; ++m)
-                v[m] = cmul(v[m], twiddle(tw, POW2 ? (k * m) << lgtw : k * m * twstep, inv));
-        }
+        if (k > 0) twiddle_all<R>(v, tw, POW2 ? k << lgtw : k * twstep, inv);
         dft<R>(v, inv, tw, n);
         if (last) {
 #pragma unroll
@@ -324,41 +354,6 @@ __device__ __forceinline__ void first(float2 *buf, const float2 *__restrict__ tw
     __syncthreads();
 }
 
-// v[m] *= w^m for m = 1..R-1, w = exp(-+ 2 pi i e / n).  The table holds w^m
-// to half an ulp, but a warp's loads of w^m for m > 1 scatter over many
-// sectors; so only w and w^4 are read and the other powers are products of
-// them (at most five roundings: RMS error about 7e-8 against 2e-8 for the
-// table, far below the FP32 transform's own rounding).
-template <int R>
-__device__ __forceinline__ void twiddle_all(float2 *v, const float2 *__restrict__ tw, int e, bool inv) {
-    using fftdev::cmul;
-    if constexpr (R == 16 || R == 8) {
-        const float2 w1 = fftdev::twiddle(tw, e, inv), w4 = fftdev::twiddle(tw, 4 * e, inv);
-        const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-        v[1] = cmul(v[1], w1);
-        v[2] = cmul(v[2], w2);
-        v[3] = cmul(v[3], w3);
-        v[4] = cmul(v[4], w4);
-        v[5] = cmul(v[5], cmul(w4, w1));
-        v[6] = cmul(v[6], cmul(w4, w2));
-        v[7] = cmul(v[7], cmul(w4, w3));
-        if constexpr (R == 16) {
-            const float2 w8 = cmul(w4, w4), w12 = cmul(w8, w4);
-            v[8] = cmul(v[8], w8);
-            v[9] = cmul(v[9], cmul(w8, w1));
-            v[10] = cmul(v[10], cmul(w8, w2));
-            v[11] = cmul(v[11], cmul(w8, w3));
-            v[12] = cmul(v[12], w12);
-            v[13] = cmul(v[13], cmul(w12, w1));
-            v[14] = cmul(v[14], cmul(w12, w2));
-            v[15] = cmul(v[15], cmul(w12, w3));
-        }
-    } else {
-#pragma unroll
-        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], fftdev::twiddle(tw, e * m, inv));
-    }
-}
-
 // Later stage of radix R over span L (constant): in place, or to store() if LAST.
 template <int N, int COUNT, int R, int L, bool LAST, class Store>
 __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
@@ -386,7 +381,7 @@ __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw
         float2 v[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = x[at(pbase, base, m)];
-        if (k > 0) twiddle_all<R>(v, tw, k << lgtw, inv);
+        if (k > 0) fftdev::twiddle_all<R>(v, tw, k << lgtw, inv);
         fftdev::dft<R>(v, inv, tw, N);
         if constexpr (LAST) {
 #pragma unroll

@@ -532,7 +532,7 @@ ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64
     {
         StageTimer t(p, s, WS_STAGE_BIN, M > 0 ? 6 : 3);
         if ((e = launch_bin(p, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: binning kernels");
-        if ((e = launch_mark(p, M, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy kernel");
+        if ((e = launch_mark_grid(p, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy kernel");
     }
     const int total = p->L.ntt * TT;
     const int nchunks = (total + p->P - 1) / p->P;

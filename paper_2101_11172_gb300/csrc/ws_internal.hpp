@@ -119,6 +119,7 @@ cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis
                         bool grid, cudaStream_t s);
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
 cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s);
+cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s);
 cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s);
 cudaError_t launch_unfold(const ws_plan_s *p, const double *uvw, int64_t M, float2 *vis, cudaStream_t s);

@@ -161,6 +161,21 @@ __global__ void mark_kernel(Launch L, const VisRec *__restrict__ rec, int64_t M,
     }
 }
 
+// Gridding's occupancy needs no pass over the visibilities: the tile lists
+// hold every (visibility, tile) pair a footprint makes, so a tile is touched
+// exactly when its list is not empty.
+__global__ void occ_from_lists_kernel(Launch L, const uint32_t *__restrict__ offsets, int64_t ntiles,
+                                      uint8_t *__restrict__ tile_occ, uint8_t *__restrict__ col_occ) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const bool occ = offsets[t + 1] != offsets[t];
+    tile_occ[t] = occ ? 1 : 0;
+    if (occ) {
+        const int64_t c = (t / ((int64_t)L.ntu * L.ntv)) * L.ntu + t % L.ntu;
+        if (!col_occ[c]) col_occ[c] = 1;
+    }
+}
+
 // Exclusive scan of n uint32 (n <= 4096 * 4096): per-block scan of 4096
 // elements, scan of the block sums in one block, then add back.
 constexpr int kScanThreads = 1024;
@@ -491,6 +506,14 @@ cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s) {
     e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
     if (e != cudaSuccess || M == 0) return e;
     mark_kernel<<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_tile_occ, p->d_col_occ);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
+    if (e != cudaSuccess) return e;
+    occ_from_lists_kernel<<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_offsets, p->ntiles,
+                                                                      p->d_tile_occ, p->d_col_occ);
     return cudaGetLastError();
 }
 
