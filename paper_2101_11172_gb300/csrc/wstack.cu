@@ -303,13 +303,19 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     float *wt = swt[warp];
     for (uint32_t e = beg + warp; e < end; e += kGridThreads / 32) {
         const VisRec r = rec[list[e]];
-        for (int l = lane; l < 3 * W; l += 32) {
-            const int axis = l / W;
-            const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
-            float acc = scoef[kMaxDeg][l];
+        // slot lane, and slot lane + 32 where 3W > 32 (W >= 11)
 #pragma unroll
-            for (int m = kMaxDeg - 1; m >= 0; --m) acc = fmaf(acc, nu, scoef[m][l]);
-            wt[l] = acc;
+        for (int h = 0; h < 2; ++h) {
+            const int l = lane + 32 * h;
+            if (h == 1 && 3 * W <= 32) break;
+            if (l < 3 * W) {
+                const int axis = l / W;
+                const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
+                float acc = scoef[kMaxDeg][l];
+#pragma unroll
+                for (int m = kMaxDeg - 1; m >= 0; --m) acc = fmaf(acc, nu, scoef[m][l]);
+                wt[l] = acc;
+            }
         }
         __syncwarp();
         // the part of the W x W x W footprint inside this tile: taps along u and v
