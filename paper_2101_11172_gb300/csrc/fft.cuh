@@ -154,29 +154,35 @@ __device__ __forceinline__ void dft<7>(float2 *v, bool inv, const float2 *__rest
 // sectors; so only w and w^4 are read and the other powers are products of
 // them (at most five roundings: RMS error about 7e-8 against 2e-8 for the
 // table, far below the FP32 transform's own rounding).
+// The same with w and w^4 given (R = 16 or 8).
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 *v, float2 w1, float2 w4) {
+    static_assert(R == 16 || R == 8, "radix 16 or 8");
+    const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+    v[1] = cmul(v[1], w1);
+    v[2] = cmul(v[2], w2);
+    v[3] = cmul(v[3], w3);
+    v[4] = cmul(v[4], w4);
+    v[5] = cmul(v[5], cmul(w4, w1));
+    v[6] = cmul(v[6], cmul(w4, w2));
+    v[7] = cmul(v[7], cmul(w4, w3));
+    if constexpr (R == 16) {
+        const float2 w8 = cmul(w4, w4), w12 = cmul(w8, w4);
+        v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], cmul(w8, w1));
+        v[10] = cmul(v[10], cmul(w8, w2));
+        v[11] = cmul(v[11], cmul(w8, w3));
+        v[12] = cmul(v[12], w12);
+        v[13] = cmul(v[13], cmul(w12, w1));
+        v[14] = cmul(v[14], cmul(w12, w2));
+        v[15] = cmul(v[15], cmul(w12, w3));
+    }
+}
+
 template <int R>
 __device__ __forceinline__ void twiddle_all(float2 *v, const float2 *__restrict__ tw, int e, bool inv) {
     if constexpr (R == 16 || R == 8) {
-        const float2 w1 = twiddle(tw, e, inv), w4 = twiddle(tw, 4 * e, inv);
-        const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1);
-        v[1] = cmul(v[1], w1);
-        v[2] = cmul(v[2], w2);
-        v[3] = cmul(v[3], w3);
-        v[4] = cmul(v[4], w4);
-        v[5] = cmul(v[5], cmul(w4, w1));
-        v[6] = cmul(v[6], cmul(w4, w2));
-        v[7] = cmul(v[7], cmul(w4, w3));
-        if constexpr (R == 16) {
-            const float2 w8 = cmul(w4, w4), w12 = cmul(w8, w4);
-            v[8] = cmul(v[8], w8);
-            v[9] = cmul(v[9], cmul(w8, w1));
-            v[10] = cmul(v[10], cmul(w8, w2));
-            v[11] = cmul(v[11], cmul(w8, w3));
-            v[12] = cmul(v[12], w12);
-            v[13] = cmul(v[13], cmul(w12, w1));
-            v[14] = cmul(v[14], cmul(w12, w2));
-            v[15] = cmul(v[15], cmul(w12, w3));
-        }
+        twiddle_powers<R>(v, twiddle(tw, e, inv), twiddle(tw, 4 * e, inv));
     } else {
 #pragma unroll
         for (int m = 1; m < R; ++m) v[m] = cmul(v[m], twiddle(tw, e * m, inv));
@@ -355,9 +361,23 @@ __device__ __forceinline__ void first(float2 *buf, const float2 *__restrict__ tw
 }
 
 // Later stage of radix R over span L (constant): in place, or to store() if LAST.
+// Twiddle bases w, w^4 of the one butterfly a thread owns in a later stage
+// (one transform, nthr >= N / R): they do not change from transform to
+// transform, so a kernel that loops over many transforms reads them once.
+struct StageTw {
+    float2 w1, w4;
+};
+
+template <int N, int R, int L>
+__device__ __forceinline__ StageTw stage_twiddles(const float2 *__restrict__ tw, bool inv, int tid) {
+    constexpr int lgtw = ilog2(N / (R * L));
+    const int k = tid & (L - 1);
+    return StageTw{fftdev::twiddle(tw, k << lgtw, inv), fftdev::twiddle(tw, (4 * k) << lgtw, inv)};
+}
+
 template <int N, int COUNT, int R, int L, bool LAST, class Store>
 __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
-                                      Store &store) {
+                                      Store &store, const StageTw *pre = nullptr) {
     using Ly = Layout<N>;
     constexpr int nb = N / R, total = COUNT * nb;
     constexpr int lgL = ilog2(L), lgtw = ilog2(N / (R * L));
@@ -381,7 +401,14 @@ __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw
         float2 v[R];
 #pragma unroll
         for (int m = 0; m < R; ++m) v[m] = x[at(pbase, base, m)];
-        if (k > 0) fftdev::twiddle_all<R>(v, tw, k << lgtw, inv);
+        if (k > 0) {
+            if constexpr (R == 16 || R == 8) {
+                if (pre) fftdev::twiddle_powers<R>(v, pre->w1, pre->w4);
+                else fftdev::twiddle_all<R>(v, tw, k << lgtw, inv);
+            } else {
+                fftdev::twiddle_all<R>(v, tw, k << lgtw, inv);
+            }
+        }
         fftdev::dft<R>(v, inv, tw, N);
         if constexpr (LAST) {
 #pragma unroll
@@ -429,23 +456,27 @@ __device__ __forceinline__ void first_inplace(float2 *buf, const float2 *__restr
 // order (see first_inplace); later stages as in fft_static.
 template <int N, class Between, class Store>
 __device__ __forceinline__ void fft_static_inplace(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid,
-                                                   int nthr, Between between, Store store) {
+                                                   int nthr, Between between, Store store,
+                                                   const fftst::StageTw &s2, const fftst::StageTw &s3) {
     using Rd = fftst::Radices<N>;
     static_assert(Rd::n == 3, "three-stage plans only");
     fftst::first_inplace<N>(buf, tw, inv, tid, between);
-    fftst::later<N, 1, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store);
-    fftst::later<N, 1, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store);
+    fftst::later<N, 1, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store, &s2);
+    fftst::later<N, 1, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store, &s3);
 }
 
 // COUNT transforms of the compile-time size N (see fft_many for the contract).
+// s2, s3: the thread's twiddle bases of stages 2 and 3 (stage_twiddles), for
+// COUNT = 1 callers that transform many sequences; null reads them per call.
 template <int N, int COUNT, class Load, class Store>
 __device__ __forceinline__ void fft_static(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
-                                           Load load, Store store) {
+                                           Load load, Store store, const fftst::StageTw *s2 = nullptr,
+                                           const fftst::StageTw *s3 = nullptr) {
     using Rd = fftst::Radices<N>;
     static_assert(Rd::n == 3, "three-stage plans only");
     fftst::first<N, COUNT>(buf, tw, inv, tid, nthr, load);
-    fftst::later<N, COUNT, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store);
-    fftst::later<N, COUNT, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store);
+    fftst::later<N, COUNT, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store, s2);
+    fftst::later<N, COUNT, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store, s3);
 }
 
 }  // namespace ws

@@ -57,6 +57,12 @@ fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
         zrow[jj] = zsplit[pix0 + jj];
     }
     int occ_tt = -1;
+    fftst::StageTw s2{}, s3{};                                  // the thread's twiddle bases, read once
+    if constexpr (NP >= 512) {
+        using Rd = fftst::Radices<NP>;
+        s2 = fftst::stage_twiddles<NP, Rd::r1, Rd::r0>(tw, false, tid);
+        s3 = fftst::stage_twiddles<NP, Rd::r2, Rd::r0 * Rd::r1>(tw, false, tid);
+    }
     for (int p = p_begin; p < p_end; ++p) {
         const int pl = plane0 + p;
         const float t = (float)(pl + L.t_lo);
@@ -80,7 +86,10 @@ fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
         auto store = [&](int, int R, float2 v) {
             if (occ[R / TU]) __stcs(plane + tiled_index(ii, R, Np), v);
         };
-        plane_fft<NP, 1>(sbuf, F, tw, false, tid, kRowThreads, load, store);
+        if constexpr (NP >= 512)
+            fft_static<NP, 1>(sbuf, tw, false, tid, kRowThreads, load, store, &s2, &s3);
+        else
+            plane_fft<NP, 1>(sbuf, F, tw, false, tid, kRowThreads, load, store);
     }
 }
 
@@ -194,6 +203,9 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
             zrow[jj] = zsplit[pix0 + jj];
             srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
         }
+        using Rd = fftst::Radices<NP>;
+        const fftst::StageTw s2 = fftst::stage_twiddles<NP, Rd::r1, Rd::r0>(tw, true, tid);
+        const fftst::StageTw s3 = fftst::stage_twiddles<NP, Rd::r2, Rd::r0 * Rd::r1>(tw, true, tid);
         if (nvalid > 0) prefetch(0);
         __syncthreads();
         for (int p = 0; p < nvalid; ++p) {
@@ -212,7 +224,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 kahan_add(a.y, a.w, v.x * sn + v.y * cs);
                 srow[jj] = a;
             };
-            fft_static_inplace<NP>(sbuf + (p & 1) * S, tw, true, tid, kRowThreads, between, store);
+            fft_static_inplace<NP>(sbuf + (p & 1) * S, tw, true, tid, kRowThreads, between, store, s2, s3);
         }
         __syncthreads();
         for (int jj = tid; jj < N; jj += kRowThreads) {
