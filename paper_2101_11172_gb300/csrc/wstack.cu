@@ -22,6 +22,16 @@
 namespace ws {
 namespace {
 
+// An integer-valued double (|x| < 1e15) modulo n in [0, n): integer arithmetic,
+// with the division only for the rare points more than a grid away.
+__device__ __forceinline__ int wrap_index(double x, int n) {
+    long long i = (long long)x;
+    if (i < -n || i >= 2LL * n) i %= n;
+    if (i < 0) i += n;
+    if (i >= n) i -= n;
+    return (int)i;
+}
+
 // ---------------------------------------------------------------------------
 // Pre-processing (Section 3.3 tap rule, Section 5.2 scaling and pre-phase)
 // ---------------------------------------------------------------------------
@@ -60,12 +70,8 @@ __global__ void prep_kernel(Launch L, const double *__restrict__ uvw, const floa
     }
     const double fu = floor(up + 0.5 * W), fv = floor(vp + 0.5 * W);
     const double ru = fu - (W - 1), rv = fv - (W - 1);
-    const double Np = (double)L.Np;
-    double mu = fmod(ru, Np), mv = fmod(rv, Np);     // exact for integer-valued doubles
-    if (mu < 0.0) mu += Np;
-    if (mv < 0.0) mv += Np;
-    r.r0 = (int)mu;
-    r.s0 = (int)mv;
+    r.r0 = wrap_index(ru, L.Np);
+    r.s0 = wrap_index(rv, L.Np);
     r.t0 = (int)t0;
     r.nux = (float)(up + 0.5 * (W - 1) - fu);
     r.nuy = (float)(vp + 0.5 * (W - 1) - fv);
