@@ -301,6 +301,25 @@ def run_reference(args):
     return 0
 
 
+# -- replicas: one process per GPU, each with its own copy of the workload ----------------
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The slowest rank's time (a no-op without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    on = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=on)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(m_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job visibilities per second: every rank's visibilities over the slowest rank's time."""
+    return m_per_rank * world / (ms_max / 1e3)
+
+
 # -- the batched serving workload -----------------------------------------------
 
 def run_batched(args):
@@ -473,11 +492,8 @@ def main():
         barrier()
     ms = start.elapsed_time(stop) / args.steps
     st = plan.stats(reset=True)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = M * world / (ms / 1e3)
+    ms = max_over_ranks(ms, dev)
+    value = replica_value(M, world, ms)
 
     # end to end: pinned host inputs -> device -> both calls -> results back to pinned host
     h_uvw = torch.from_numpy(wl.uvw).pin_memory()
@@ -507,10 +523,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms_e2e = e0.elapsed_time(e1) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ms_e2e, dev)
     h2d = wl.uvw.nbytes + M * 8 + wl.N * wl.N * 8
     d2h = M * 8 + wl.N * wl.N * 8
     plan.stats(reset=True)
@@ -586,7 +599,7 @@ def main():
                                            "planes_per_chunk": plan.planes_per_chunk,
                                            "real_sky_folding": bool(args.real_sky),
                                            "parallelism": f"replicas x{world}"}),
-            "e2e": {"value": M * world / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": replica_value(M, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
             "gpu_launches": None,
             "roofline": roof, "stages": stages, "accuracy": acc, "clocks": clocks.summary(),
