@@ -495,34 +495,56 @@ def main():
     ms = max_over_ranks(ms, dev)
     value = replica_value(M, world, ms)
 
-    # end to end: pinned host inputs -> device -> both calls -> results back to pinned host
+    # end to end: pinned host inputs -> device -> both calls -> results back to pinned host,
+    # pipelined over two buffer sets: step i+1's inputs go up and step i-1's results come
+    # down on a copy stream while step i computes; every step's copies are inside the timing
     h_uvw = torch.from_numpy(wl.uvw).pin_memory()
     h_vis = torch.from_numpy(wl.vis.astype(np.complex64)).pin_memory()
     h_img = torch.from_numpy(wl.image.astype(np.complex64)).pin_memory()
     h_vout = torch.empty(M, dtype=torch.complex64).pin_memory()
     h_dout = torch.empty(wl.N, wl.N, dtype=torch.complex64).pin_memory()
-    plan_e2e = plan
-    d_uvw, d_vis, d_img = torch.empty_like(uvw), torch.empty_like(vis), torch.empty_like(img)
+    cs = torch.cuda.Stream(dev)
+    d_in = [(torch.empty_like(uvw), torch.empty_like(vis), torch.empty_like(img)) for _ in range(2)]
+    d_out = [(torch.empty_like(vout), torch.empty_like(dout)) for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step():
-        d_uvw.copy_(h_uvw, non_blocking=True)
-        d_vis.copy_(h_vis, non_blocking=True)
-        d_img.copy_(h_img, non_blocking=True)
-        plan_e2e.degrid(d_img, d_uvw, out=vout)
-        plan_e2e.grid(d_uvw, d_vis, out=dout)
-        h_vout.copy_(vout, non_blocking=True)
-        h_dout.copy_(dout, non_blocking=True)
+    def upload(j):
+        b = j % 2
+        with torch.cuda.stream(cs):
+            cs.wait_event(ev_done[b])                # the step that last read buffer set b is done
+            for d, h in zip(d_in[b], (h_uvw, h_vis, h_img)):
+                d.copy_(h, non_blocking=True)
+            ev_in[b].record(cs)
 
-    e2e_step()
+    def run_e2e(nsteps):
+        upload(0)
+        for i in range(nsteps):
+            if i + 1 < nsteps:
+                upload(i + 1)
+            b = i % 2
+            stream.wait_event(ev_in[b])
+            du, dv, di = d_in[b]
+            vo, do = d_out[b]
+            plan.degrid(di, du, out=vo)
+            plan.grid(du, dv, out=do)
+            ev_done[b].record(stream)
+            with torch.cuda.stream(cs):
+                cs.wait_event(ev_done[b])
+                h_vout.copy_(vo, non_blocking=True)
+                h_dout.copy_(do, non_blocking=True)
+        stream.wait_stream(cs)
+
+    run_e2e(2)
     torch.cuda.synchronize(dev)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.e2e_steps):
-        e2e_step()
+    cs.wait_event(e0)
+    run_e2e(max(2, args.e2e_steps))
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    ms_e2e = e0.elapsed_time(e1) / args.e2e_steps
+    ms_e2e = e0.elapsed_time(e1) / max(2, args.e2e_steps)
     ms_e2e = max_over_ranks(ms_e2e, dev)
     h2d = wl.uvw.nbytes + M * 8 + wl.N * wl.N * 8
     d2h = M * 8 + wl.N * wl.N * 8
@@ -600,7 +622,8 @@ def main():
                                            "real_sky_folding": bool(args.real_sky),
                                            "parallelism": f"replicas x{world}"}),
             "e2e": {"value": replica_value(M, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+                    "copies": "pinned host <-> device on a second stream, overlapping the neighbouring steps"},
             "gpu_launches": None,
             "roofline": roof, "stages": stages, "accuracy": acc, "clocks": clocks.summary(),
             "real_sky_folded": folded,

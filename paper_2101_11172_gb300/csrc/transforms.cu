@@ -45,11 +45,13 @@ const tf::Ops &ops_for(int Np, bool mixed) {
 }
 }  // namespace
 
-int fft_threads() { return tf::kThreads; }
-int fft_per_cta() { return tf::kPerCta; }
-
+// Largest dynamic shared memory any transform kernel of this plan asks for
+// (the compile-time inv_rows double buffer is checked by its own setup).
 size_t transform_smem_bytes(const FftPlan &F, int N) {
-    return tf::smem2(F) > tf::smem_rows(F, N) ? tf::smem2(F) : tf::smem_rows(F, N);
+    size_t b = tf::smem2(F);
+    if (tf::smem_rows(F, N) > b) b = tf::smem_rows(F, N);
+    if (tf::smem_fwd_rows(F, N) > b) b = tf::smem_fwd_rows(F, N);
+    return b;
 }
 
 cudaError_t setup_transform_kernels(const FftPlan &F, int N) {

@@ -127,8 +127,6 @@ cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64
                                 float2 *vis, cudaStream_t s);
 
 // Plane transforms (transforms.cu).
-int fft_threads();
-int fft_per_cta();
 size_t transform_smem_bytes(const FftPlan &F, int N);
 cudaError_t setup_transform_kernels(const FftPlan &F, int N);
 cudaError_t launch_fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
