@@ -209,21 +209,25 @@ def traffic_for(stage: str, workload: str, planes: int):
 
 # -- the oracle on a bounded slab ---------------------------------------------------
 
-def _oracle_slab_run(wl, g_full, lm, t_a, n_vis, rng):
+def _oracle_slab_run(wl, g_full, lm, t_a, n_vis, rng, N=None):
     """Oracle grid + degrid over the W planes t_a .. t_a+W-1 for n_vis visibilities
-    whose footprints start at plane t_a; returns (seconds, visibilities used)."""
+    whose footprints start at plane t_a, on the workload's image (or, for the
+    per-visibility rate, on an N x N image of the same field, whose planes cost
+    next to nothing); returns (seconds, visibilities used)."""
     import numpy as np
 
     from oracle import wstack as ows
     from oracle.geometry import first_tap, make_geometry
+    N = wl.N if N is None else N
     t0 = first_tap(wl.uvw[:, 2] * g_full.nscale, wl.W)[0]
     pool = np.nonzero(t0 == t_a)[0]
     sel = rng.choice(pool, min(n_vis, pool.size), replace=False)
     w_lo = (t_a + wl.W / 2.0 - 0.5) / g_full.nscale          # first tap of w_lo is t_a
-    g = make_geometry(wl.N, wl.x0, wl.W, wl.fov, w_lo, w_lo)
+    g = make_geometry(N, wl.x0, wl.W, wl.fov, w_lo, w_lo)
     assert (g.t_lo, g.t_hi) == (t_a, t_a + wl.W - 1)
+    image = wl.image if N == wl.N else np.ones((N, N), dtype=np.complex128)
     t = time.perf_counter()
-    ows.degrid(g, lm, wl.image, wl.uvw[sel])
+    ows.degrid(g, lm, image, wl.uvw[sel])
     ows.grid(g, lm, wl.uvw[sel], wl.vis[sel])
     return time.perf_counter() - t, sel.size
 
@@ -234,13 +238,15 @@ class OracleRate:
     The oracle's work is one N' x N' transform, crop and screen per w-plane
     and one W^3 spread / gather per visibility, so its time for the full job
     is ``planes x c_plane + M x c_vis``.  Both rates are measured on the
-    minimal slab of W planes in the middle of the w-range: ``calibrate`` runs
-    it with a small and a larger set of visibilities whose footprints lie in
-    the slab (c_vis from the difference); ``step`` re-times the small run and
-    returns the extrapolated visibilities per second.
+    minimal slab of W planes in the middle of the w-range, with visibilities
+    whose footprints lie in the slab.  ``calibrate`` takes c_vis from the
+    difference of two runs (m_small and m_large visibilities) on a 64 x 64
+    image of the same field, where the planes cost milliseconds and cannot
+    drown the difference; ``step`` times the workload's own image with
+    m_small visibilities for c_plane and returns the extrapolated rate.
     """
 
-    def __init__(self, wl, m_small=1000, m_large=5000):
+    def __init__(self, wl, m_small=1000, m_large=20000):
         import numpy as np
 
         from oracle.geometry import make_geometry
@@ -256,8 +262,8 @@ class OracleRate:
         ows.correction(self.g, self.lm)      # the per-image product is plan work: made once, outside the timing
 
     def calibrate(self):
-        t_s, n_s = _oracle_slab_run(self.wl, self.g, self.lm, self.t_a, self.m_small, self.rng)
-        t_l, n_l = _oracle_slab_run(self.wl, self.g, self.lm, self.t_a, self.m_large, self.rng)
+        t_s, n_s = _oracle_slab_run(self.wl, self.g, self.lm, self.t_a, self.m_small, self.rng, N=64)
+        t_l, n_l = _oracle_slab_run(self.wl, self.g, self.lm, self.t_a, self.m_large, self.rng, N=64)
         self.c_vis = max(0.0, (t_l - t_s) / max(1, n_l - n_s))
         return t_s + t_l
 
@@ -271,7 +277,8 @@ class OracleRate:
     def sample(self):
         t_s, c_plane = self.last
         return (f"slab of {self.wl.W} of {self.g.Nw} w-planes (t = {self.t_a}..{self.t_a + self.wl.W - 1}) with "
-                f"{self.m_small} and {self.m_large} visibilities starting there: {c_plane:.2f} s per plane, "
+                f"{self.m_small} visibilities starting there; per-visibility rate from {self.m_small} and "
+                f"{self.m_large} visibilities on a 64 x 64 image: {c_plane:.2f} s per plane, "
                 f"{1e3 * self.c_vis:.3f} ms per visibility (grid + degrid), extrapolated to "
                 f"{self.g.Nw} planes and {self.wl.M} visibilities")
 
