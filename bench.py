@@ -180,11 +180,13 @@ def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int,
 
 
 def library_source_sha() -> str:
-    """Hash of every CUDA/C++ source of the library (any kernel change invalidates counters)."""
+    """Hash of the library's device code (the kernels, and the headers that shape their
+    arguments): any change there invalidates the DRAM counters of profiles/traffic.json.
+    Host-only files (plan construction, batches, the least-misfit fit) are left out."""
     import glob
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2101_11172_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".hpp", ".cpp")):
+        if f.endswith((".cu", ".cuh")) or os.path.basename(f) in ("ws_internal.hpp", "fft_plan.hpp"):
             with open(f, "rb") as fh:
                 h.update(fh.read())
     return h.hexdigest()
