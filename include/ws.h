@@ -61,11 +61,14 @@ enum {
     WS_FLAG_ASYNC = 1u << 0,       /* do not wait for the stream at the end of each call */
     WS_FLAG_NO_Z_OFFSET = 1u << 1, /* Eq. n_params_no_offset: n0 = 1, z in [-z0, 0] */
     WS_FLAG_TIMING = 1u << 2,      /* record CUDA events around every stage (see ws_plan_stats) */
-    WS_FLAG_HERMITIAN = 1u << 3    /* real sky (Section 5.4): a visibility at w < 0 is handled as the
+    WS_FLAG_HERMITIAN = 1u << 3,   /* real sky (Section 5.4): a visibility at w < 0 is handled as the
                                       conjugate visibility at (-u, -v, -w), so only |w| needs planes.
                                       ws_degrid reads only the real part of the image; ws_grid returns
                                       the real dirty image Re(sum_k V_k exp(+2 pi i ...)) with a zero
                                       imaginary part.  The plan's w-range is folded the same way. */
+    WS_FLAG_DIVIDE_BY_N = 1u << 4  /* images are the sky brightness I rather than f = I / n (Section 5.2):
+                                      ws_degrid uses I / n and ws_grid returns its dirty image divided
+                                      by n, which keeps the two adjoint */
 };
 
 /* Stages of one call, in execution order (Algorithm 5 / Algorithm 6 steps). */

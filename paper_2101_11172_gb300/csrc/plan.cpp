@@ -298,7 +298,8 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         set_error("ws_plan: need finite w_min <= w_max");
         return WS_ERR_ARG;
     }
-    if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_TIMING | WS_FLAG_HERMITIAN)) {
+    if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_TIMING | WS_FLAG_HERMITIAN |
+                            WS_FLAG_DIVIDE_BY_N)) {
         set_error("ws_plan: unknown flag bits");
         return WS_ERR_ARG;
     }
@@ -435,11 +436,13 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
             const double rr = l * l + m * m;
             const double nm1 = -rr / (1.0 + std::sqrt(1.0 - rr));
             double z = (nm1 + (1.0 - n0)) / nscale;
+            // Section 5.2: the operators act on f = I / n; WS_FLAG_DIVIDE_BY_N folds the 1/n in here
+            const double inv_n = (flags & WS_FLAG_DIVIDE_BY_N) ? 1.0 / (1.0 + nm1) : 1.0;
             if (orig_bins > 0) {
-                corr[(size_t)i * N + j] = (float)(hx[i] * hx[j]);      // Algorithm 3 step 5: 2-D correction
+                corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * inv_n);   // Algorithm 3 step 5: 2-D correction
             } else {
                 z = std::min(std::max(z, -p->x0), p->x0);
-                corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * h_series(p->fit, z));
+                corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * h_series(p->fit, z) * inv_n);
             }
             const double hi = std::nearbyint(z * 8192.0) / 8192.0;
             zs[(size_t)i * N + j] = make_float2((float)hi, (float)(z - hi));

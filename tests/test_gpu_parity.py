@@ -140,6 +140,22 @@ def test_hermitian_folding_real_sky(dev):
     assert abs(lhs - rhs) < 2e-6 * np.linalg.norm(v) * np.linalg.norm(c["vis"])
 
 
+def test_divide_by_n_acts_on_the_sky_brightness(dev):
+    # Section 5.2: f = I / n.  With WS_FLAG_DIVIDE_BY_N the calls take I and return the dirty
+    # image divided by n: degrid(I) = plain degrid(I / n), grid(V) = plain grid(V) / n.
+    from oracle.geometry import n_minus_one
+    from paper_2101_11172_gb300 import WS_FLAG_DIVIDE_BY_N
+    c = case(N=128, M=4000, fov=0.8, seed=29)
+    g = make_geometry(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"])
+    l = g.pixel_lm()
+    n = 1.0 + n_minus_one(l[None, :], l[:, None])
+    v1, d1, _ = run_gpu(c, dev, flags=WS_FLAG_DIVIDE_BY_N)
+    c0 = dict(c, image=c["image"] / n)
+    v0, d0, _ = run_gpu(c0, dev)
+    assert rel(v1, v0) < 1e-6 and rel(d1, d0 / n) < 1e-6
+    assert abs(np.vdot(v1, c["vis"]) - np.vdot(c["image"], d1)) < 2e-6 * abs(np.vdot(v1, c["vis"]))
+
+
 def test_edge_counts_and_drops(dev):
     from paper_2101_11172_gb300 import _lib
     from paper_2101_11172_gb300.wstack import Plan
