@@ -50,7 +50,7 @@ const tf::Ops &ops_for(int Np, bool mixed) {
 size_t transform_smem_bytes(const FftPlan &F, int N) {
     size_t b = tf::smem2(F);
     if (tf::smem_rows(F, N) > b) b = tf::smem_rows(F, N);
-    if (tf::smem_fwd_rows(F, N) > b) b = tf::smem_fwd_rows(F, N);
+    if (tf::smem_fwd_rows(F, N, false) > b) b = tf::smem_fwd_rows(F, N, false);
     return b;
 }
 

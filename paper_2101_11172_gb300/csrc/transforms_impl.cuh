@@ -32,10 +32,20 @@ __device__ __forceinline__ void plane_fft(float2 *buf, const FftPlan &F, const f
 
 // -- degridding --------------------------------------------------------------
 
+// Planes per exact evaluation of the screen in fwd_rows: in between, each
+// pixel's screened value advances one plane by a product with exp(-2 pi i z).
+constexpr int kScreenSteps = 8;
+
 // One CTA owns image row ii for a run of planes: the corrected row and its z
 // stay in shared memory, so each plane costs the screen, one FFT and the
 // stores of the strips some footprint reads.
-template <int NP>
+//
+// STEP keeps two more shared rows, the screened row g = row x exp(-2 pi i t z)
+// and the step exp(-2 pi i z).  g is evaluated exactly on every kScreenSteps-th
+// plane of the CTA's share; on the planes between, the FFT's first stage reads
+// g and leaves g x step in its place for the next plane.  Each pixel is read
+// by the same thread on every plane, so the update needs no barrier.
+template <int NP, bool STEP>
 __global__ void __launch_bounds__(kRowThreads, 2)
 fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ img,
                 const float2 *__restrict__ zsplit, const uint8_t *__restrict__ col_occ, int plane0, int planes,
@@ -44,7 +54,9 @@ fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
     const int Np = L.Np, N = L.N, half = N / 2;
     float2 *irow = sbuf + F.stride;                              // N (F.stride is even: 16-byte aligned)
     float2 *zrow = irow + N;                                     // N
-    uint8_t *occ = reinterpret_cast<uint8_t *>(zrow + N);        // ntu: strips of the current t-tile
+    float2 *grow = zrow + N;                                     // N, STEP only: the screened row
+    float2 *erow = grow + N;                                     // N, STEP only: exp(-2 pi i z)
+    uint8_t *occ = reinterpret_cast<uint8_t *>(irow + (STEP ? 4 : 2) * N);   // ntu: strips of the current t-tile
     const int ii = blockIdx.x, tid = threadIdx.x;
     // this CTA's planes: an equal share of the chunk's valid planes
     const int nvalid = min(planes, L.Nw - plane0);
@@ -54,7 +66,13 @@ fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
     const size_t pix0 = (size_t)ii * N;
     for (int jj = tid; jj < N; jj += kRowThreads) {
         irow[jj] = img[pix0 + jj];
-        zrow[jj] = zsplit[pix0 + jj];
+        const float2 z = zsplit[pix0 + jj];
+        zrow[jj] = z;
+        if constexpr (STEP) {
+            float sn, cs;
+            phase_tz(1.f, z, &sn, &cs);
+            erow[jj] = make_float2(cs, -sn);
+        }
     }
     int occ_tt = -1;
     fftst::StageTw s2{}, s3{};                                  // the thread's twiddle bases, read once
@@ -74,13 +92,34 @@ fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
             occ_tt = tt;
             __syncthreads();
         }
+        // row x exp(-i phi), phi = 2 pi t z
+        auto screened = [&](int jj) -> float2 {
+            const float2 f = irow[jj];
+            float sn, cs;
+            phase_tz(t, zrow[jj], &sn, &cs);
+            return make_float2(f.x * cs + f.y * sn, f.y * cs - f.x * sn);
+        };
+        bool step = false;                   // uniform: advance g to the next plane
+        if constexpr (STEP) {
+            if ((p - p_begin) % kScreenSteps == 0) {
+                for (int jj = tid; jj < N; jj += kRowThreads) grow[jj] = screened(jj);
+                __syncthreads();
+            }
+            step = (p + 1 - p_begin) % kScreenSteps != 0 && p + 1 < p_end;
+        }
         auto load = [&](int, int J) -> float2 {
             if (!in_crop(J, half, Np)) return make_float2(0.f, 0.f);
             const int jj = grid_to_crop(J, half, Np);
-            const float2 g = irow[jj];
-            float sn, cs;
-            phase_tz(t, zrow[jj], &sn, &cs);                     // times exp(-i phi)
-            return make_float2(g.x * cs + g.y * sn, g.y * cs - g.x * sn);
+            if constexpr (!STEP) {
+                return screened(jj);
+            } else {
+                const float2 g = grow[jj];
+                if (step) {
+                    const float2 e = erow[jj];
+                    grow[jj] = make_float2(g.x * e.x - g.y * e.y, g.x * e.y + g.y * e.x);
+                }
+                return g;
+            }
         };
         // columns of this plane's t-tile that no footprint touches are never read
         auto store = [&](int, int R, float2 v) {
@@ -286,9 +325,13 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
 
 // transform buffers + one occupancy byte per strip (at most N'/16 or N'/32 of them)
 inline size_t smem2(const FftPlan &F) { return (size_t)kPerCta * F.stride * sizeof(float2) + F.n / TU + 16; }
-inline size_t smem_fwd_rows(const FftPlan &F, int N) {
-    return (size_t)F.stride * sizeof(float2) + (size_t)N * 2 * sizeof(float2) + F.n / TU + 16;
+inline size_t smem_fwd_rows(const FftPlan &F, int N, bool step) {
+    return (size_t)F.stride * sizeof(float2) + (size_t)N * (step ? 4 : 2) * sizeof(float2) + F.n / TU + 16;
 }
+// fwd_rows steps its screen where the two extra rows still leave room for two
+// CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
+constexpr size_t kTwoCtaSmem = 113 * 1024;
+inline bool fwd_rows_step(const FftPlan &F, int N) { return smem_fwd_rows(F, N, true) <= kTwoCtaSmem; }
 // CTAs per image row in fwd_rows: enough rows x groups for about eight CTAs per SM
 inline int row_groups(int N, int planes, int sms) {
     const int want = (8 * sms + N - 1) / N;
@@ -324,15 +367,23 @@ template <int NP>
 struct Transforms {
     static cudaError_t setup(const FftPlan &F, int N) {
         cudaError_t e;
-        if ((e = allow_smem(fwd_rows_kernel<NP>, smem_fwd_rows(F, N))) != cudaSuccess) return e;
+        if ((e = allow_smem(fwd_rows_kernel<NP, false>, smem_fwd_rows(F, N, false))) != cudaSuccess) return e;
+        if (fwd_rows_step(F, N) && (e = allow_smem(fwd_rows_kernel<NP, true>, smem_fwd_rows(F, N, true))) != cudaSuccess)
+            return e;
         if ((e = allow_smem(fwd_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
         if ((e = allow_smem(inv_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
         return allow_smem(inv_rows_kernel<NP>, smem_inv_rows<NP>(F, N));
     }
     static cudaError_t fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
-        fwd_rows_kernel<NP><<<dim3(p->L.N, row_groups(p->L.N, planes, p->sms)), kRowThreads, smem_fwd_rows(p->fft, p->L.N),
-                              s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit, p->d_col_occ, chunk * p->P, planes,
-                                   p->d_stack);
+        const bool step = fwd_rows_step(p->fft, p->L.N);
+        const dim3 grid(p->L.N, row_groups(p->L.N, planes, p->sms));
+        const size_t smem = smem_fwd_rows(p->fft, p->L.N, step);
+        if (step)
+            fwd_rows_kernel<NP, true><<<grid, kRowThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit,
+                                                                      p->d_col_occ, chunk * p->P, planes, p->d_stack);
+        else
+            fwd_rows_kernel<NP, false><<<grid, kRowThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit,
+                                                                       p->d_col_occ, chunk * p->P, planes, p->d_stack);
         return cudaGetLastError();
     }
     static cudaError_t fwd_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
