@@ -149,7 +149,9 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
 
 /* Algorithm 5: vis (device complex64 M, read) at uvw (device double M x 3) ->
  * dirty (device complex64 N x N, overwritten).  Out-of-range visibilities are
- * skipped and counted as for ws_degrid. */
+ * skipped and counted as for ws_degrid.  The row transforms of N' = 512 ..
+ * 4096 wait for their TMA row copies with a bounded wait; a wait that gives up
+ * leaves dirty incomplete and the call returns WS_ERR_TIMEOUT. */
 ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
                   void *dirty, ws_stream_t stream);
 

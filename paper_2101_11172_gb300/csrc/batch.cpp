@@ -132,7 +132,8 @@ ws_status capture(ws_batch_s *b, int dir, const std::vector<const void *> &ptr, 
             st = enqueue_degrid(p, static_cast<const float2 *>(a), static_cast<const double *>(c), b->M[i],
                                 static_cast<float2 *>(out), s);
         if (st == WS_OK) {
-            e = cudaMemcpyAsync(p->h_drop, p->d_drop, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(p->h_drop, p->d_drop, kCounters * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                s);
             if (e != cudaSuccess) st = cuda_fail(e, "ws_batch: reading drop counters");
         }
     }
@@ -228,6 +229,11 @@ ws_status run(ws_batch_s *b, int dir, const std::vector<const void *> &ptr, cuda
     if (e != cudaSuccess) return cuda_fail(e, "ws_batch: waiting for the stream");
     for (size_t i = 0; i < b->plans.size(); ++i) {
         const ws_plan_s *p = b->plans[i];
+        if (p->h_drop[2]) {
+            set_error("instance " + std::to_string(i) + ": " + std::to_string(p->h_drop[2]) +
+                      " device waits for copies gave up; the output is incomplete");
+            return WS_ERR_TIMEOUT;
+        }
         if (p->h_drop[0] || p->h_drop[1]) {
             set_error("instance " + std::to_string(i) + ": " + std::to_string(p->h_drop[0] + p->h_drop[1]) +
                       " visibilities were dropped (" + (p->h_drop[0] ? "non-finite u, v" : "w outside the range") +

@@ -423,12 +423,13 @@ __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw
 
 // First stage for inputs already in the buffer, in natural order at 0..N-1
 // (one transform, at most one butterfly per thread: nthr >= N / R0).  Each
-// thread reads the R0 inputs m (N/R0) + tid, the CTA synchronises, between()
+// thread reads the R0 inputs m (N/R0) + tid (input m is zero where bit m of
+// live is clear, whatever the buffer holds), the CTA synchronises, between()
 // runs (the buffer's old contents are dead by then), and the outputs go to
 // their padded digit-reversed slots.
 template <int N, class Between>
 __device__ __forceinline__ void first_inplace(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid,
-                                              Between &between) {
+                                              Between &between, uint32_t live) {
     using Rd = Radices<N>;
     using Ly = Layout<N>;
     constexpr int R = Rd::r0, nb = N / R;
@@ -436,7 +437,10 @@ __device__ __forceinline__ void first_inplace(float2 *buf, const float2 *__restr
     float2 v[R];
     if (active) {
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = buf[m * nb + tid];
+        for (int m = 0; m < R; ++m) {
+            const float2 x = buf[m * nb + tid];
+            v[m] = (live >> m) & 1u ? x : make_float2(0.f, 0.f);
+        }
     }
     __syncthreads();
     between();
@@ -453,14 +457,15 @@ __device__ __forceinline__ void first_inplace(float2 *buf, const float2 *__restr
 }  // namespace fftst
 
 // One transform of the compile-time size N whose input sits in buf in natural
-// order (see first_inplace); later stages as in fft_static.
+// order (see first_inplace for live); later stages as in fft_static.
 template <int N, class Between, class Store>
 __device__ __forceinline__ void fft_static_inplace(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid,
                                                    int nthr, Between between, Store store,
-                                                   const fftst::StageTw &s2, const fftst::StageTw &s3) {
+                                                   const fftst::StageTw &s2, const fftst::StageTw &s3,
+                                                   uint32_t live = 0xffffffffu) {
     using Rd = fftst::Radices<N>;
     static_assert(Rd::n == 3, "three-stage plans only");
-    fftst::first_inplace<N>(buf, tw, inv, tid, between);
+    fftst::first_inplace<N>(buf, tw, inv, tid, between, live);
     fftst::later<N, 1, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store, &s2);
     fftst::later<N, 1, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store, &s3);
 }

@@ -194,13 +194,17 @@ bool fft_make_plan(int n, FftPlan *F) {
 }
 
 ws_status finish_call(ws_plan_s *p, cudaStream_t s) {
-    cudaError_t e = cudaMemcpyAsync(p->h_drop, p->d_drop, 2 * sizeof(unsigned long long),
+    cudaError_t e = cudaMemcpyAsync(p->h_drop, p->d_drop, kCounters * sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "reading the drop counters");
     if (p->flags & WS_FLAG_ASYNC) return WS_OK;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "waiting for the stream");
     p->last_dropped = (int64_t)(p->h_drop[0] + p->h_drop[1]);
+    if (p->h_drop[2]) {
+        set_error(std::to_string(p->h_drop[2]) + " device waits for copies gave up; the output is incomplete");
+        return WS_ERR_TIMEOUT;
+    }
     if (p->h_drop[0]) {
         set_error(std::to_string(p->h_drop[0]) + " visibilities had non-finite or huge u, v and were dropped");
         return WS_ERR_UV_RANGE;
@@ -511,9 +515,9 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     WS_TRY(dev_alloc(&p->d_tile_occ, (size_t)p->ntiles, &p->bytes), "allocating tile occupancy");
     WS_TRY(dev_alloc(&p->d_col_occ, (size_t)L.ntt * L.ntu, &p->bytes), "allocating strip occupancy");
     WS_TRY(dev_alloc(&p->d_img, (size_t)N * N, &p->bytes), "allocating the corrected image");
-    WS_TRY(dev_alloc(&p->d_drop, (size_t)2, &p->bytes), "allocating drop counters");
-    WS_TRY(cudaMallocHost((void **)&p->h_drop, 2 * sizeof(unsigned long long)), "allocating pinned counters");
-    std::memset(p->h_drop, 0, 2 * sizeof(unsigned long long));
+    WS_TRY(dev_alloc(&p->d_drop, (size_t)kCounters, &p->bytes), "allocating drop counters");
+    WS_TRY(cudaMallocHost((void **)&p->h_drop, kCounters * sizeof(unsigned long long)), "allocating pinned counters");
+    std::memset(p->h_drop, 0, kCounters * sizeof(unsigned long long));
 #undef WS_TRY
     *out = p;
     return WS_OK;
@@ -525,7 +529,7 @@ fail:
 
 ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, float2 *dirty,
                        cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, 2 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, kCounters * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "ws_grid: clearing counters");
     p->stats.calls += 1;
     {
@@ -562,7 +566,7 @@ ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64
 
 ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, int64_t M, float2 *vis,
                          cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, 2 * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, kCounters * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "ws_degrid: clearing counters");
     if (M == 0) return WS_OK;
     if ((e = cudaMemsetAsync(vis, 0, (size_t)M * sizeof(float2), s)) != cudaSuccess)

@@ -22,6 +22,45 @@
 namespace ws {
 
 namespace tf {
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+EncodeTiled encode_tiled() {
+    static const EncodeTiled fn = []() -> EncodeTiled {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiled>(f);
+    }();
+    return fn;
+}
+}  // namespace
+
+// Element (S, R) of plane p sits at float offset 2 (((R / 4) N' + S) 4 + R % 4)
+// + 2 N'^2 p: dimension 0 runs over the 8 floats of a block row, 1 over the
+// N' rows S (32 bytes apart), 2 over the N'/4 column blocks (32 N' bytes
+// apart), 3 over the P planes.  A box {8, 1, 4, 1} is one strip of TU = 16
+// columns of one row, 128 contiguous bytes in shared memory in column order.
+cudaError_t row_tensor_map(const ws_plan_s *p, CUtensorMap *map) {
+    const EncodeTiled encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t Np = (cuuint64_t)p->L.Np;
+    const cuuint64_t dims[4] = {2 * CB, Np, Np / CB, (cuuint64_t)p->P};
+    const cuuint64_t strides[3] = {2 * CB * sizeof(float), Np * 2 * CB * sizeof(float), Np * Np * sizeof(float2)};
+    const cuuint32_t box[4] = {2 * CB, 1, (cuuint32_t)std::min<cuuint64_t>(256, Np / CB), 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->d_stack, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 const Ops &ops_runtime_pow2() {
     static const Ops o = ops_of<0>();
     return o;

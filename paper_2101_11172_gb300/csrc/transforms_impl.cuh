@@ -5,6 +5,8 @@
 // fft.cuh.  Each translation unit instantiates Transforms<NP> for its sizes.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "ws_internal.hpp"
@@ -184,28 +186,73 @@ inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
     plane_fft<NP, kPerCta>(sbuf, F, tw, true, threadIdx.x, kThreads, load, store);
 }
 
-// Asynchronous 8-byte copy global -> shared; src_bytes = 0 writes zeros and reads nothing.
-__device__ __forceinline__ void cp_async8(float2 *dst, const float2 *src, bool read) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(read ? 8 : 0) : "memory");
+// -- TMA row copies and mbarriers ----------------------------------------------
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for the phase of the given parity to complete, giving up after about
+// 2^20 polls (a few hundred milliseconds): false if it did not complete.
+constexpr int kWaitPolls = 1 << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    for (int i = 0; i < kWaitPolls; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+// Box of an image row: {8 floats, 1 row, min(256, N'/4) column blocks, 1 plane}
+// of the stack's row map.
+__device__ __forceinline__ void tma_row_box(float2 *dst, const CUtensorMap *map, int row, int block, int plane,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(block), "r"(plane), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Shared-memory layout of the compile-time inv_rows: two 128-byte aligned row
+// buffers (TMA destinations), z row, compensated sums, two mbarriers.
+template <int NP>
+struct RowsSmem {
+    static constexpr size_t buf = (fftst::Layout<NP>::stride * sizeof(float2) + 127) / 128 * 128;
+    static size_t bytes(int N) { return 128 + 2 * buf + (size_t)N * (sizeof(float2) + sizeof(float4)) + 16; }
+};
 
 // One CTA owns image row ii and sums the chunk's planes into a compensated
 // accumulator in shared memory; the last FFT stage screens and accumulates.
 //
-// Compile-time plans double-buffer the row: while plane p is transformed in
-// one buffer, plane p + 1 is copied into the other with cp.async (zeros for
-// strips no footprint touched), so the loads of the next plane overlap the
-// arithmetic of this one.  Each thread copies exactly the elements it reads
-// in the first stage, so its own wait on the copies is enough.
+// Compile-time plans double-buffer the row with TMA: as plane p starts, warp
+// 0 copies plane p + 1's row into the other buffer in boxes of up to 256
+// column blocks (8 KB), all completing on that buffer's mbarrier.  Strips no
+// footprint touched hold stale data; the first FFT stage masks them to zero.
+// Every wait is bounded; a CTA that gives up counts the failure in *timeouts,
+// waits (bounded) for the copy in flight and returns.
 template <int NP>
 __global__ void __launch_bounds__(kRowThreads, 2)
 inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ stack,
-                const uint8_t *__restrict__ col_occ, int plane0, int planes, const float2 *__restrict__ zsplit,
-                const float *__restrict__ corr, float4 *__restrict__ acc, int first, int last,
-                float2 *__restrict__ dirty) {
+                const __grid_constant__ CUtensorMap row_map, const uint8_t *__restrict__ col_occ, int plane0,
+                int planes, const float2 *__restrict__ zsplit, const float *__restrict__ corr,
+                float4 *__restrict__ acc, int first, int last, float2 *__restrict__ dirty,
+                unsigned long long *__restrict__ timeouts) {
     extern __shared__ __align__(16) float2 sbuf[];
     const int Np = L.Np, N = L.N, half = N / 2;
     const int ii = blockIdx.x;
@@ -213,31 +260,33 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
     const size_t pix0 = (size_t)ii * N;
     const int nvalid = min(planes, L.Nw - plane0);
     if constexpr (NP >= 512) {
-        constexpr int S = fftst::Layout<NP>::stride;             // even: every region stays 16-byte aligned
+        using Sm = RowsSmem<NP>;
         constexpr int R0 = fftst::Radices<NP>::r0, nb = NP / R0;
-        float2 *zrow = sbuf + 2 * S;                             // N
-        float4 *srow = reinterpret_cast<float4 *>(zrow + N);     // N: (sum re, sum im, comp re, comp im)
-        uint32_t mask = 0;                                       // strips of this thread's elements, one t-tile
-        int mask_tt = -1;
-        auto prefetch = [&](int p) {
-            const int tt = (plane0 + p) / TT;
-            float2 *dst = sbuf + (p & 1) * S;
-            const float2 *plane = stack + (size_t)p * Np * Np;
-            if (tid < nb) {
-                if (tt != mask_tt) {
-                    mask = 0;
-#pragma unroll
-                    for (int m = 0; m < R0; ++m) mask |= (uint32_t)(__ldg(col_occ + tt * L.ntu + (m * nb + tid) / TU) != 0) << m;
-                    mask_tt = tt;
-                }
-#pragma unroll
-                for (int m = 0; m < R0; ++m) {
-                    const int R = m * nb + tid;
-                    cp_async8(dst + R, plane + tiled_index(ii, R, Np), (mask >> m) & 1u);
-                }
-            }
-            cp_async_commit();
+        constexpr int kBoxBlocks = NP / CB < 256 ? NP / CB : 256, kRowBoxes = NP / CB / kBoxBlocks;
+        // 128-byte aligned start, by pointer arithmetic on sbuf so that every
+        // access below stays a shared-memory access
+        float2 *base = sbuf + ((128u - (smem_addr(sbuf) & 127u)) & 127u) / sizeof(float2);
+        constexpr int kBuf = (int)(Sm::buf / sizeof(float2));
+        auto row_buf = [&](int p) { return base + (p & 1) * kBuf; };
+        float2 *zrow = base + 2 * kBuf;                                   // N
+        float4 *srow = reinterpret_cast<float4 *>(zrow + N);              // N: (sum re, sum im, comp re, comp im)
+        uint64_t *bar = reinterpret_cast<uint64_t *>(srow + N);           // 2
+        const int warp = tid >> 5, lane = tid & 31;
+        // warp 0: copy plane p's row ii into buffer p & 1, kRowBoxes boxes of
+        // kBoxBlocks column blocks (strips no footprint touched come along and
+        // are masked to zero by the first stage)
+        auto issue = [&](int p) {
+            fence_proxy_async();             // the buffer's last generic reads precede these writes
+            if (lane == 0) mbar_arrive_expect_tx(&bar[p & 1], (unsigned)(NP * sizeof(float2)));
+            __syncwarp();
+            if (lane < kRowBoxes)
+                tma_row_box(row_buf(p) + lane * kBoxBlocks * CB, &row_map, ii, lane * kBoxBlocks, p, &bar[p & 1]);
         };
+        if (tid == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            mbar_init_fence();
+        }
         for (int jj = tid; jj < N; jj += kRowThreads) {
             zrow[jj] = zsplit[pix0 + jj];
             srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
@@ -245,14 +294,34 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
         using Rd = fftst::Radices<NP>;
         const fftst::StageTw s2 = fftst::stage_twiddles<NP, Rd::r1, Rd::r0>(tw, true, tid);
         const fftst::StageTw s3 = fftst::stage_twiddles<NP, Rd::r2, Rd::r0 * Rd::r1>(tw, true, tid);
-        if (nvalid > 0) prefetch(0);
         __syncthreads();
+        if (warp == 0 && nvalid > 0) issue(0);
+        uint32_t live = 0;                   // strips of this thread's first-stage inputs, one t-tile
+        int live_tt = -1;
         for (int p = 0; p < nvalid; ++p) {
             const float t = (float)(plane0 + p + L.t_lo);
-            cp_async_wait_all();
-            auto between = [&]() {
-                if (p + 1 < nvalid) prefetch(p + 1);
-            };
+            const int tt = (plane0 + p) / TT;
+            if (tt != live_tt) {             // threads past nb own no first-stage butterfly
+                live = 0;
+                if (tid < nb) {
+#pragma unroll
+                    for (int m = 0; m < R0; ++m)
+                        live |= (uint32_t)(__ldg(col_occ + tt * L.ntu + (m * nb + tid) / TU) != 0) << m;
+                }
+                live_tt = tt;
+            }
+            const bool ok = mbar_wait(&bar[p & 1], (p >> 1) & 1);
+            if (__syncthreads_or(!ok)) {     // uniform: give up on this row
+                if (tid == 0) {
+                    atomicAdd(timeouts, 1ull);
+                    mbar_wait(&bar[p & 1], (p >> 1) & 1);
+                }
+                __syncthreads();
+                return;
+            }
+            // every thread is past plane p - 1, so its buffer is free for plane p + 1
+            if (warp == 0 && p + 1 < nvalid) issue(p + 1);
+            auto between = [] {};
             auto store = [&](int, int J, float2 v) {
                 if (!in_crop(J, half, Np)) return;
                 const int jj = grid_to_crop(J, half, Np);
@@ -263,7 +332,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 kahan_add(a.y, a.w, v.x * sn + v.y * cs);
                 srow[jj] = a;
             };
-            fft_static_inplace<NP>(sbuf + (p & 1) * S, tw, true, tid, kRowThreads, between, store, s2, s3);
+            fft_static_inplace<NP>(row_buf(p), tw, true, tid, kRowThreads, between, store, s2, s3, live);
         }
         __syncthreads();
         for (int jj = tid; jj < N; jj += kRowThreads) {
@@ -340,11 +409,11 @@ inline int row_groups(int N, int planes, int sms) {
 inline size_t smem_rows(const FftPlan &F, int N) {
     return (size_t)F.stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4)) + F.n / TU + 16;
 }
-// inv_rows: compile-time plans keep two row buffers and no occupancy bytes
+// inv_rows: compile-time plans keep two aligned row buffers and two mbarriers
 template <int NP>
 inline size_t smem_inv_rows(const FftPlan &F, int N) {
     if constexpr (NP >= 512)
-        return (size_t)2 * fftst::Layout<NP>::stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4));
+        return RowsSmem<NP>::bytes(N);
     else
         return smem_rows(F, N);
 }
@@ -361,6 +430,10 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
     if (bytes > (size_t)optin) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
+
+// The stack as a 4-D FP32 tensor for TMA row copies: {8 floats of a column
+// block's row, N' rows, N'/4 blocks, P planes}, boxes of one strip.
+cudaError_t row_tensor_map(const ws_plan_s *p, CUtensorMap *map);
 
 // Launchers of one FFT variant.
 template <int NP>
@@ -398,9 +471,14 @@ struct Transforms {
     }
     static cudaError_t inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
                                 cudaStream_t s) {
+        CUtensorMap map{};
+        if constexpr (NP >= 512) {
+            const cudaError_t e = row_tensor_map(p, &map);
+            if (e != cudaSuccess) return e;
+        }
         inv_rows_kernel<NP><<<p->L.N, kRowThreads, smem_inv_rows<NP>(p->fft, p->L.N), s>>>(
-            p->L, p->fft, p->d_tw, p->d_stack, p->d_col_occ, chunk * p->P, planes, p->d_zsplit, p->d_corr,
-            p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty);
+            p->L, p->fft, p->d_tw, p->d_stack, map, p->d_col_occ, chunk * p->P, planes, p->d_zsplit, p->d_corr,
+            p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty, p->d_drop + 2);
         return cudaGetLastError();
     }
 };

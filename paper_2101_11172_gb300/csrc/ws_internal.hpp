@@ -21,6 +21,9 @@ constexpr int TV = 32;
 constexpr int TT = 8;
 constexpr int kMaxW = 12;
 constexpr int kMaxDeg = 16;
+// Per-call device counters: visibilities dropped for non-finite u, v; for w
+// outside the plan's range; and bounded device waits that gave up.
+constexpr int kCounters = 3;
 
 // One visibility after pre-processing: first grid point of its W x W x W
 // footprint (u and v wrapped into [0, N'), t relative to the plan's t_lo;
@@ -82,7 +85,7 @@ struct ws_plan_s {
     uint8_t *d_col_occ = nullptr;  // ntt x ntu: 1 if any tile of that (t-tile, u-tile) strip is touched
     float4 *d_acc = nullptr;       // N x N: (sum re, sum im, comp re, comp im)
     float2 *d_img = nullptr;       // N x N: corrected image (degridding)
-    unsigned long long *d_drop = nullptr;   // [0] = non-finite uv, [1] = w out of range
+    unsigned long long *d_drop = nullptr;   // kCounters: [0] non-finite uv, [1] w out of range, [2] timed-out waits
     unsigned long long *h_drop = nullptr;   // pinned mirror
     int64_t last_dropped = 0;
     int64_t bytes = 0;
