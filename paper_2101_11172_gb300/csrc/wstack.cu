@@ -277,31 +277,33 @@ __device__ __forceinline__ void red_add_shared(float *addr, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(addr)), "f"(v) : "memory");
 }
 
+template <int W>
 __global__ void __launch_bounds__(kGridThreads, 5)
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
               uint32_t tile_base, int chunk_tt0, float2 *__restrict__ stack) {
-    __shared__ float sre[kTileSlots];
-    __shared__ float sim[kTileSlots];
-    __shared__ float swt[kGridThreads / 32][3 * kMaxW];
-    __shared__ float scoef[kMaxDeg + 1][3 * kMaxW];   // [m][slot]: weight slot l's polynomial, zero-padded
+    __shared__ __align__(16) float sre[kTileSlots];
+    __shared__ __align__(16) float sim[kTileSlots];
+    __shared__ float swt[kGridThreads / 32][3 * W];
+    __shared__ float scoef[kMaxDeg + 1][3 * W];       // [m][slot]: weight slot l's polynomial, zero-padded
     const uint32_t tile = tile_base + blockIdx.x;
     if (offsets[tile] == offsets[tile + 1]) return;   // empty tile: the transforms treat it as zero
     const int tu = tile % L.ntu;
     const int tv = (tile / L.ntu) % L.ntv;
     const int tt = tile / (L.ntu * L.ntv);
-    for (int i = threadIdx.x; i < kTileSlots; i += kGridThreads) {
-        sre[i] = 0.f;
-        sim[i] = 0.f;
+    static_assert(kTileSlots % 4 == 0, "the tile is cleared in float4 stores");
+    for (int i = threadIdx.x; i < kTileSlots / 4; i += kGridThreads) {
+        reinterpret_cast<float4 *>(sre)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4 *>(sim)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const int W = L.W, Np = L.Np;
+    const int Np = L.Np;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // weight slot l < 3W is (axis l / W, tap l % W); lane l evaluates slots l and
     // l + 32.  coef holds the (u, v) table and then the w table, W x (deg + 1) each.
-    for (int i = threadIdx.x; i < (kMaxDeg + 1) * 3 * kMaxW; i += kGridThreads) {
-        const int m = i / (3 * kMaxW), l = i % (3 * kMaxW), axis = l / W, tap = l - axis * W;
+    for (int i = threadIdx.x; i < (kMaxDeg + 1) * 3 * W; i += kGridThreads) {
+        const int m = i / (3 * W), l = i % (3 * W), axis = l / W, tap = l - axis * W;
         const int row = (axis == 2 ? W : 0) + tap;
-        scoef[m][l] = (l < 3 * W && m <= deg) ? coef[row * (deg + 1) + m] : 0.f;
+        scoef[m][l] = m <= deg ? coef[row * (deg + 1) + m] : 0.f;
     }
     __syncthreads();
     const uint32_t beg = offsets[tile], end = offsets[tile + 1];
@@ -311,9 +313,8 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
         const VisRec r = rec[list[e]];
         // slot lane, and slot lane + 32 where 3W > 32 (W >= 11)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < (3 * W + 31) / 32; ++h) {
             const int l = lane + 32 * h;
-            if (h == 1 && 3 * W <= 32) break;
             if (l < 3 * W) {
                 const int axis = l / W;
                 const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
@@ -534,8 +535,28 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
     const int chunk_tt0 = chunk * (p->P / TT);
     const uint32_t tile_base = (uint32_t)chunk_tt0 * tiles_per_tt;
     const unsigned nblocks = (unsigned)(planes / TT) * tiles_per_tt;
-    grid3d_kernel<<<nblocks, kGridThreads, 0, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list,
-                                                  tile_base, chunk_tt0, p->d_stack);
+#define WS_GRID_CASE(w)                                                                                       \
+    case w:                                                                                                  \
+        grid3d_kernel<w><<<nblocks, kGridThreads, 0, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets,  \
+                                                          p->d_list, tile_base, chunk_tt0, p->d_stack);        \
+        break;
+    switch (p->L.W) {
+        WS_GRID_CASE(1)
+        WS_GRID_CASE(2)
+        WS_GRID_CASE(3)
+        WS_GRID_CASE(4)
+        WS_GRID_CASE(5)
+        WS_GRID_CASE(6)
+        WS_GRID_CASE(7)
+        WS_GRID_CASE(8)
+        WS_GRID_CASE(9)
+        WS_GRID_CASE(10)
+        WS_GRID_CASE(11)
+        WS_GRID_CASE(12)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef WS_GRID_CASE
     return cudaGetLastError();
 }
 
