@@ -93,6 +93,29 @@ def test_plane_chunks_agree(dev, monkeypatch):
     assert rel(v2, v_ref) < REL_TOL and rel(d2, d_ref) < REL_TOL
 
 
+@pytest.mark.parametrize("N", [256, 512])
+def test_compile_time_plans_against_oracle(dev, N):
+    # N' = 512 and 1024 run the compile-time FFT plans: TMA row copies in
+    # inv_rows (first-stage butterflies for only 32 or 64 of the 256 threads),
+    # the stepped screen in fwd_rows (several CTAs per row, 8-plane runs)
+    c = case(N=N, M=3000, W=7, seed=21)
+    v, d, g, *_ = check_against_oracle(c, dev)
+    assert g.Np == 2 * N
+
+
+def test_compile_time_plan_chunks_agree(dev, monkeypatch):
+    # several chunks on a compile-time plan: TMA plane coordinates relative to
+    # the chunk and the compensated sum carried between inv_rows launches
+    c = case(N=256, M=3000, W=7, seed=22)
+    v1, d1, i1 = run_gpu(c, dev)
+    monkeypatch.setenv("WS_PLANES_PER_CHUNK", "8")
+    v2, d2, i2 = run_gpu(c, dev)
+    assert i1["Np"] == 512 and i1["P"] >= i1["Nw"] and i2["P"] == 8 and i2["Nw"] > 24
+    assert rel(v2, v1) < 1e-6 and rel(d2, d1) < 1e-6
+    g, lm, v_ref, d_ref = oracle_pair(c)
+    assert rel(v2, v_ref) < REL_TOL and rel(d2, d_ref) < REL_TOL
+
+
 def test_wraparound_at_grid_edge(dev):
     # u' within W/2 of +-N'/2: taps wrap onto the opposite edge; the periodic
     # inverse DFT keeps the result exact (compare with the DFT directly).
