@@ -278,7 +278,7 @@ __device__ __forceinline__ void red_add_shared(float *addr, float v) {
 }
 
 template <int W>
-__global__ void __launch_bounds__(kGridThreads, 5)
+__global__ void __launch_bounds__(kGridThreads, 6)
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
               uint32_t tile_base, int chunk_tt0, float2 *__restrict__ stack) {
