@@ -121,32 +121,70 @@ __device__ __forceinline__ void dft<16>(float2 *v, bool inv, const float2 *__res
     for (int i = 0; i < 16; ++i) v[i] = o[i];
 }
 
-// Odd radices: direct R-point DFT with roots of unity from the table.
+// cos and sin of 2 pi m / R for the odd radices R = 3, 5, 7 and 0 <= m < R
+// (decimal expansions of the closed forms; sin is odd in m about R / 2).
+__host__ __device__ constexpr double odd_cos(int R, int m) {
+    const int k = m <= R / 2 ? m : R - m;
+    return k == 0 ? 1.0
+         : R == 3 ? -0.5
+         : R == 5 ? (k == 1 ? 0.30901699437494742 : -0.80901699437494742)
+         : (k == 1 ? 0.62348980185873353 : k == 2 ? -0.22252093395631440 : -0.90096886790241913);
+}
+__host__ __device__ constexpr double odd_sin(int R, int m) {
+    const int k = m <= R / 2 ? m : R - m;
+    const double s = k == 0 ? 0.0
+                   : R == 3 ? 0.86602540378443865
+                   : R == 5 ? (k == 1 ? 0.95105651629515357 : 0.58778525229247313)
+                   : (k == 1 ? 0.78183148246802981 : k == 2 ? 0.97492791218182361 : 0.43388373911755812);
+    return m <= R / 2 ? s : -s;
+}
+
+// Odd radix R = 2h + 1 in symmetric form.  With a_r = x_r + x_{R-r} and
+// b_r = x_r - x_{R-r} (r = 1..h): X_0 = x_0 + sum a_r and, for k = 1..h,
+// A_k = x_0 + sum_r cos(2 pi r k / R) a_r, B_k = sum_r sin(2 pi r k / R) b_r,
+// X_k = A_k - i B_k and X_{R-k} = A_k + i B_k (the signs swap for the inverse).
 template <int R>
-__device__ __forceinline__ void dft_odd(float2 *v, bool inv, const float2 *__restrict__ tw, int n) {
-    float2 o[R];
-    const int step = n / R;
+__device__ __forceinline__ void dft_odd(float2 *v, bool inv) {
+    constexpr int h = R / 2;
+    float2 a[h + 1], b[h + 1];
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        float2 acc = v[0];
-#pragma unroll
-        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], twiddle(tw, ((r * k) % R) * step, inv)));
-        o[k] = acc;
+    for (int r = 1; r <= h; ++r) {
+        a[r] = cadd(v[r], v[R - r]);
+        b[r] = csub(v[r], v[R - r]);
     }
+    const float2 x0 = v[0];
+    float2 s0 = x0;
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = o[k];
+    for (int r = 1; r <= h; ++r) s0 = cadd(s0, a[r]);
+    v[0] = s0;
+#pragma unroll
+    for (int k = 1; k <= h; ++k) {
+        float2 A = x0, B = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int r = 1; r <= h; ++r) {
+            const float c = (float)odd_cos(R, (r * k) % R), sn = (float)odd_sin(R, (r * k) % R);
+            A.x = fmaf(c, a[r].x, A.x);
+            A.y = fmaf(c, a[r].y, A.y);
+            B.x = fmaf(sn, b[r].x, B.x);
+            B.y = fmaf(sn, b[r].y, B.y);
+        }
+        const float2 minus = make_float2(A.x + B.y, A.y - B.x);   // A - i B
+        const float2 plus = make_float2(A.x - B.y, A.y + B.x);    // A + i B
+        v[k] = inv ? plus : minus;
+        v[R - k] = inv ? minus : plus;
+    }
 }
 template <>
-__device__ __forceinline__ void dft<3>(float2 *v, bool inv, const float2 *__restrict__ tw, int n) {
-    dft_odd<3>(v, inv, tw, n);
+__device__ __forceinline__ void dft<3>(float2 *v, bool inv, const float2 *__restrict__, int) {
+    dft_odd<3>(v, inv);
 }
 template <>
-__device__ __forceinline__ void dft<5>(float2 *v, bool inv, const float2 *__restrict__ tw, int n) {
-    dft_odd<5>(v, inv, tw, n);
+__device__ __forceinline__ void dft<5>(float2 *v, bool inv, const float2 *__restrict__, int) {
+    dft_odd<5>(v, inv);
 }
 template <>
-__device__ __forceinline__ void dft<7>(float2 *v, bool inv, const float2 *__restrict__ tw, int n) {
-    dft_odd<7>(v, inv, tw, n);
+__device__ __forceinline__ void dft<7>(float2 *v, bool inv, const float2 *__restrict__, int) {
+    dft_odd<7>(v, inv);
 }
 
 // v[m] *= w^m for m = 1..R-1, w = exp(-+ 2 pi i e / n).  The table holds w^m
@@ -184,8 +222,18 @@ __device__ __forceinline__ void twiddle_all(float2 *v, const float2 *__restrict_
     if constexpr (R == 16 || R == 8) {
         twiddle_powers<R>(v, twiddle(tw, e, inv), twiddle(tw, 4 * e, inv));
     } else {
-#pragma unroll
-        for (int m = 1; m < R; ++m) v[m] = cmul(v[m], twiddle(tw, e * m, inv));
+        // R <= 7: w^m from w by products, at most three roundings deep
+        static_assert(R <= 7, "radices 3 to 7");
+        const float2 w1 = twiddle(tw, e, inv), w2 = cmul(w1, w1);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        if constexpr (R >= 4) v[3] = cmul(v[3], cmul(w2, w1));
+        if constexpr (R >= 5) v[4] = cmul(v[4], cmul(w2, w2));
+        if constexpr (R >= 6) v[5] = cmul(v[5], cmul(cmul(w2, w2), w1));
+        if constexpr (R >= 7) {
+            const float2 w3 = cmul(w2, w1);
+            v[6] = cmul(v[6], cmul(w3, w3));
+        }
     }
 }
 
