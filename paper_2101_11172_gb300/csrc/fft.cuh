@@ -244,8 +244,13 @@ __device__ __forceinline__ void twiddle_all(float2 *v, const float2 *__restrict_
 // can do them one after another and a stage needs no barrier between its
 // reads and writes.  Work item q -> transform t = q % COUNT, butterfly q / COUNT.
 // POW2: n, R and L are powers of two and the index arithmetic uses shifts.
+// x / d for 0 <= x < 2^16, 1 <= d < 2^13, with mul = div_mul(d) (fft_plan.hpp)
+__device__ __forceinline__ int div_small(int x, unsigned mul) {
+    return mul ? (int)__umulhi((unsigned)x, mul) : x;
+}
+
 template <int R, int COUNT, bool POW2, class Store>
-__device__ __forceinline__ void dit_stage(float2 *buf, const FftPlan &P, int L, bool last,
+__device__ __forceinline__ void dit_stage(float2 *buf, const FftPlan &P, int L, unsigned Lmul, bool last,
                                           const float2 *__restrict__ tw, bool inv, int tid, int nthr,
                                           Store &store) {
     const int n = P.n, nb = n / R, total = COUNT * nb;
@@ -262,7 +267,7 @@ __device__ __forceinline__ void dit_stage(float2 *buf, const FftPlan &P, int L, 
             blk = bq >> logL;
             k = bq & (L - 1);
         } else {
-            blk = bq / L;
+            blk = div_small(bq, Lmul);
             k = bq - blk * L;
         }
         const int base = blk * R * L + k;
@@ -304,10 +309,12 @@ __device__ __forceinline__ void dit_first(float2 *buf, const FftPlan &P, const f
         }
         int g = 0;
         for (int i = 1; i < P.nstages; ++i) {
-            if constexpr (POW2)
+            if constexpr (POW2) {
                 g += ((j >> P.lxw[i]) & (P.radix[i] - 1)) << P.lgw[i];
-            else
-                g += ((j / P.xw[i]) % P.radix[i]) * P.gw[i];
+            } else {
+                const int a = div_small(j, P.xw_mul[i]);
+                g += (a - div_small(a, P.r_mul[i]) * P.radix[i]) * P.gw[i];
+            }
         }
         float2 *x = buf + t * P.stride;
 #pragma unroll
@@ -345,14 +352,17 @@ __device__ __forceinline__ void fft_many(float2 *buf, const FftPlan &P, const fl
         const int R = P.radix[s];
         const bool last = s == P.nstages - 1;
         switch (R) {
-            case 16: fftdev::dit_stage<16, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store); break;
-            case 8: fftdev::dit_stage<8, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store); break;
-            case 4: fftdev::dit_stage<4, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store); break;
+            case 16: fftdev::dit_stage<16, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store); break;
+            case 8: fftdev::dit_stage<8, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store); break;
+            case 4: fftdev::dit_stage<4, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store); break;
             default:
                 if constexpr (MIXED) {
-                    if (R == 7) fftdev::dit_stage<7, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store);
-                    else if (R == 5) fftdev::dit_stage<5, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store);
-                    else fftdev::dit_stage<3, COUNT, POW2>(buf, P, L, last, tw, inv, tid, nthr, store);
+                    if (R == 7)
+                        fftdev::dit_stage<7, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store);
+                    else if (R == 5)
+                        fftdev::dit_stage<5, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store);
+                    else
+                        fftdev::dit_stage<3, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store);
                 }
                 break;
         }

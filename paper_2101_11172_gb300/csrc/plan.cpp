@@ -175,6 +175,7 @@ bool fft_make_plan(int n, FftPlan *F) {
         while ((1 << l) < v) ++l;
         return (1 << l) == v ? l : -1;
     };
+    int L = 1;
     for (int i = 0; i < ns; ++i) {
         int xw = 1, gw = 1;
         for (int l = i + 1; l < ns; ++l) xw *= F->radix[l];
@@ -183,6 +184,10 @@ bool fft_make_plan(int n, FftPlan *F) {
         F->gw[i] = gw;
         F->lxw[i] = log2i(xw);
         F->lgw[i] = log2i(gw);
+        F->xw_mul[i] = div_mul(xw);
+        F->r_mul[i] = div_mul(F->radix[i]);
+        F->L_mul[i] = div_mul(L);
+        L *= F->radix[i];
     }
     F->logn = log2i(n);
     int shift = 4;
