@@ -17,6 +17,15 @@ namespace tf {
 constexpr int kThreads = 256;       // two rows or two columns per CTA
 constexpr int kPerCta = 2;
 constexpr int kRowThreads = 256;    // one row per CTA (inv_rows)
+// Shared memory per CTA that still lets two CTAs share an SM (228 KB, 1 KB of it reserved per CTA).
+constexpr size_t kTwoCtaSmem = 113 * 1024;
+
+// Runtime-plan inv_rows keeps the z row in shared memory when the row buffer,
+// the z row and the compensated sums still leave room for two CTAs per SM.
+__host__ __device__ inline bool rows_keep_z(const FftPlan &F, int N) {
+    return (size_t)F.stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4)) + F.n / TU + 16 <=
+           kTwoCtaSmem;
+}
 
 __device__ __forceinline__ int grid_to_crop(int g, int half, int Np) { return g < half ? g + half : g - (Np - half); }
 __device__ __forceinline__ bool in_crop(int g, int half, int Np) { return g < half || g >= Np - half; }
@@ -345,12 +354,16 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
             }
         }
     } else {
-        float2 *zrow = sbuf + F.stride;                          // N (F.stride is even: 16-byte aligned)
-        float4 *srow = reinterpret_cast<float4 *>(zrow + N);     // N: (sum re, sum im, comp re, comp im)
+        // the z row stays in shared memory where two CTAs per SM still fit, else
+        // the screen reads z from global memory
+        const bool keep_z = rows_keep_z(F, N);
+        float2 *zrow = sbuf + F.stride;                          // N if keep_z (F.stride is even: 16-byte aligned)
+        float4 *srow = reinterpret_cast<float4 *>(zrow + (keep_z ? N : 0));   // N: (sum re, sum im, comp re, comp im)
         uint8_t *occ = reinterpret_cast<uint8_t *>(srow + N);    // ntu: strips of the current t-tile
+        const float2 *zsrc = keep_z ? zrow : zsplit + pix0;
         int occ_tt = -1;
         for (int jj = tid; jj < N; jj += kRowThreads) {
-            zrow[jj] = zsplit[pix0 + jj];
+            if (keep_z) zrow[jj] = zsplit[pix0 + jj];
             srow[jj] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : acc[pix0 + jj];
         }
         __syncthreads();
@@ -371,7 +384,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 if (!in_crop(J, half, Np)) return;
                 const int jj = grid_to_crop(J, half, Np);
                 float sn, cs;
-                phase_tz(t, zrow[jj], &sn, &cs);
+                phase_tz(t, zsrc[jj], &sn, &cs);
                 float4 a = srow[jj];
                 kahan_add(a.x, a.z, v.x * cs - v.y * sn);
                 kahan_add(a.y, a.w, v.x * sn + v.y * cs);
@@ -398,8 +411,7 @@ inline size_t smem_fwd_rows(const FftPlan &F, int N, bool step) {
     return (size_t)F.stride * sizeof(float2) + (size_t)N * (step ? 4 : 2) * sizeof(float2) + F.n / TU + 16;
 }
 // fwd_rows steps its screen where the two extra rows still leave room for two
-// CTAs per SM (228 KB of shared memory, 1 KB of it reserved per CTA)
-constexpr size_t kTwoCtaSmem = 113 * 1024;
+// CTAs per SM
 inline bool fwd_rows_step(const FftPlan &F, int N) { return smem_fwd_rows(F, N, true) <= kTwoCtaSmem; }
 // CTAs per image row in fwd_rows: enough rows x groups for about eight CTAs per SM
 inline int row_groups(int N, int planes, int sms) {
@@ -407,7 +419,8 @@ inline int row_groups(int N, int planes, int sms) {
     return want < 1 ? 1 : (want > planes ? (planes > 0 ? planes : 1) : want);
 }
 inline size_t smem_rows(const FftPlan &F, int N) {
-    return (size_t)F.stride * sizeof(float2) + (size_t)N * (sizeof(float2) + sizeof(float4)) + F.n / TU + 16;
+    return (size_t)F.stride * sizeof(float2) + (size_t)N * ((rows_keep_z(F, N) ? sizeof(float2) : 0) + sizeof(float4)) +
+           F.n / TU + 16;
 }
 // inv_rows: compile-time plans keep two aligned row buffers and two mbarriers
 template <int NP>
