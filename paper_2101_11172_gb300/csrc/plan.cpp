@@ -583,7 +583,7 @@ ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, i
             return cuda_fail(e, "ws_degrid: prep kernel");
     }
     {
-        StageTimer t(p, s, WS_STAGE_BIN, 6);
+        StageTimer t(p, s, WS_STAGE_BIN, 7);
         if ((e = launch_bin(p, M, false, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: binning kernels");
         if ((e = launch_mark(p, M, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy kernel");
     }

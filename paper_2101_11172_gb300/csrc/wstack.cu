@@ -151,30 +151,15 @@ __global__ void scatter_kernel(Launch L, const VisRec *__restrict__ rec, int64_t
 // Occupancy of the stack: which gridding tiles, and which (t-tile, u-tile)
 // strips of N' rows, any visibility footprint touches.  Every other cell of
 // the stack is zero when gridding and never read when degridding, so the
-// plane kernels skip it.  Plain byte stores of 1 (idempotent, no atomics),
-// each preceded by a load so that the many visibilities sharing a tile do
-// not all write it.
-__global__ void mark_kernel(Launch L, const VisRec *__restrict__ rec, int64_t M, uint8_t *__restrict__ tile_occ,
-                            uint8_t *__restrict__ col_occ) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= M) return;
-    uint32_t keys[kMaxKeys];
-    int n = record_keys<true>(L, rec[k], keys);
-    for (int i = 0; i < n; ++i) {
-        if (!tile_occ[keys[i]]) tile_occ[keys[i]] = 1;
-        const uint32_t c = (keys[i] / (L.ntu * L.ntv)) * L.ntu + keys[i] % L.ntu;
-        if (!col_occ[c]) col_occ[c] = 1;
-    }
-}
-
-// Gridding's occupancy needs no pass over the visibilities: the tile lists
-// hold every (visibility, tile) pair a footprint makes, so a tile is touched
-// exactly when its list is not empty.
-__global__ void occ_from_lists_kernel(Launch L, const uint32_t *__restrict__ offsets, int64_t ntiles,
-                                      uint8_t *__restrict__ tile_occ, uint8_t *__restrict__ col_occ) {
+// plane kernels skip it.  A tile is touched exactly when some (visibility,
+// tile) pair of a footprint names it: gridding reads that from its tile
+// lists (offsets), degridding from a count of the pairs (counts).
+template <bool FROM_COUNTS>
+__global__ void occ_kernel(Launch L, const uint32_t *__restrict__ per_tile, int64_t ntiles,
+                           uint8_t *__restrict__ tile_occ, uint8_t *__restrict__ col_occ) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
-    const bool occ = offsets[t + 1] != offsets[t];
+    const bool occ = FROM_COUNTS ? per_tile[t] != 0 : per_tile[t + 1] != per_tile[t];
     tile_occ[t] = occ ? 1 : 0;
     if (occ) {
         const int64_t c = (t / ((int64_t)L.ntu * L.ntv)) * L.ntu + t % L.ntu;
@@ -513,20 +498,25 @@ cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Degridding's occupancy: count the footprints' (visibility, tile) pairs in
+// the counters the binning has finished with, then mark the tiles.
 cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_tile_occ, 0, (size_t)p->ntiles, s);
+    cudaError_t e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
-    if (e != cudaSuccess || M == 0) return e;
-    mark_kernel<<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_tile_occ, p->d_col_occ);
+    if (M == 0) return cudaMemsetAsync(p->d_tile_occ, 0, (size_t)p->ntiles, s);
+    e = cudaMemsetAsync(p->d_counts, 0, (size_t)p->ntiles * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    count_kernel<true><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts);
+    occ_kernel<true><<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_counts, p->ntiles, p->d_tile_occ,
+                                                                p->d_col_occ);
     return cudaGetLastError();
 }
 
 cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
     if (e != cudaSuccess) return e;
-    occ_from_lists_kernel<<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_offsets, p->ntiles,
-                                                                      p->d_tile_occ, p->d_col_occ);
+    occ_kernel<false><<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_offsets, p->ntiles, p->d_tile_occ,
+                                                                 p->d_col_occ);
     return cudaGetLastError();
 }
 
