@@ -16,6 +16,8 @@
 // [N'-N/2, N') and [0, N/2).  Planes use the column-block layout of common.cuh.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "ws_internal.hpp"
 
@@ -387,7 +389,7 @@ constexpr int kDegridThreads = 256;
 // flight.  The polynomial table sits in shared memory for the weights.  Each
 // chunk adds its planes' share to vis, in chunk order.
 template <int W>
-__global__ void __launch_bounds__(kDegridThreads)
+__global__ void __launch_bounds__(kDegridThreads, W <= 6 ? 5 : (W <= 8 ? 4 : 1))
 degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
                 const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_order,
                 const float2 *__restrict__ stack, int plane0, int planes, float2 *__restrict__ vis) {
@@ -396,67 +398,72 @@ degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec 
     __shared__ float scoef[2 * W * (kMaxDeg + 1)];       // (u, v) table, then the w table
     for (int i = threadIdx.x; i < 2 * W * (deg + 1); i += kDegridThreads) scoef[i] = coef[i];
     __syncthreads();
-    const int64_t widx = ((int64_t)blockIdx.x * kDegridThreads + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (widx >= (int64_t)*n_order) return;      // entries of the sorted list (dropped ones excluded)
-    const uint32_t k = order[widx];
-    const VisRec r = rec[k];
-    if (r.t0 < 0) return;
+    const int64_t n = (int64_t)*n_order;                   // entries of the sorted list (dropped ones excluded)
+    const int64_t nwarps = (int64_t)gridDim.x * (kDegridThreads / 32);
     const int Np = L.Np;
-    const int c_lo = max(0, plane0 - r.t0);
-    const int c_hi = min(W - 1, plane0 + planes - 1 - r.t0);
-    if (c_lo > c_hi) return;
-    float *wt = swt[warp];
-    for (int l = lane; l < 3 * W; l += 32) {                 // 3W > 32 for W >= 11
-        const int axis = l / W, i = l - axis * W;
-        const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
-        const float *c = scoef + ((axis == 2 ? W : 0) + i) * (deg + 1);
-        float acc = c[deg];
-        for (int m = deg - 1; m >= 0; --m) acc = fmaf(acc, nu, c[m]);
-        wt[l] = acc;
-    }
-    __syncwarp();
     const size_t plane = (size_t)Np * Np;
-    const int64_t t_rel = (int64_t)r.t0 - plane0;           // stack plane of tap c is t_rel + c
-    float2 f[kPasses][W];
-#pragma unroll
-    for (int ps = 0; ps < kPasses; ++ps) {
-        const int pair = lane + 32 * ps;
-        const int a = pair % W, b = pair / W;
-        const bool live = pair < W * W;
-        const float2 *cell = stack + tiled_index(wrap_add(r.s0, live ? b : 0, Np), wrap_add(r.r0, a, Np), Np);
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            f[ps][c] = make_float2(0.f, 0.f);
-            if (live && c >= c_lo && c <= c_hi) f[ps][c] = __ldg(cell + (size_t)(t_rel + c) * plane);
+    float *wt = swt[warp];
+    // a grid of resident CTAs: each warp takes every nwarps-th visibility of the
+    // tile-sorted list, so the warps in flight still gather from neighbouring cells
+    for (int64_t widx = ((int64_t)blockIdx.x * kDegridThreads + threadIdx.x) >> 5; widx < n; widx += nwarps) {
+        const uint32_t k = order[widx];
+        const VisRec r = rec[k];
+        if (r.t0 < 0) continue;
+        const int c_lo = max(0, plane0 - r.t0);
+        const int c_hi = min(W - 1, plane0 + planes - 1 - r.t0);
+        if (c_lo > c_hi) continue;
+        __syncwarp();                                       // the previous visibility's weights are read
+        for (int l = lane; l < 3 * W; l += 32) {             // 3W > 32 for W >= 11
+            const int axis = l / W, i = l - axis * W;
+            const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
+            const float *c = scoef + ((axis == 2 ? W : 0) + i) * (deg + 1);
+            float acc = c[deg];
+            for (int m = deg - 1; m >= 0; --m) acc = fmaf(acc, nu, c[m]);
+            wt[l] = acc;
         }
-    }
-    float ar = 0.f, ai = 0.f;
+        __syncwarp();
+        const int64_t t_rel = (int64_t)r.t0 - plane0;       // stack plane of tap c is t_rel + c
+        float2 f[kPasses][W];
 #pragma unroll
-    for (int ps = 0; ps < kPasses; ++ps) {
-        const int pair = lane + 32 * ps;
-        if (pair >= W * W) break;
-        const int a = pair % W, b = pair / W;
-        float sr = 0.f, si = 0.f;
+        for (int ps = 0; ps < kPasses; ++ps) {
+            const int pair = lane + 32 * ps;
+            const int a = pair % W, b = pair / W;
+            const bool live = pair < W * W;
+            const float2 *cell = stack + tiled_index(wrap_add(r.s0, live ? b : 0, Np), wrap_add(r.r0, a, Np), Np);
 #pragma unroll
-        for (int c = 0; c < W; ++c) {
-            const float wc = wt[2 * W + c];
-            sr = fmaf(wc, f[ps][c].x, sr);
-            si = fmaf(wc, f[ps][c].y, si);
+            for (int c = 0; c < W; ++c) {
+                f[ps][c] = make_float2(0.f, 0.f);
+                if (live && c >= c_lo && c <= c_hi) f[ps][c] = __ldg(cell + (size_t)(t_rel + c) * plane);
+            }
         }
-        const float wab = wt[a] * wt[W + b];
-        ar = fmaf(wab, sr, ar);
-        ai = fmaf(wab, si, ai);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        ar += __shfl_xor_sync(0xffffffffu, ar, o);
-        ai += __shfl_xor_sync(0xffffffffu, ai, o);
-    }
-    if (lane == 0) {
-        float2 out = vis[k];
-        out.x += ar * r.vre - ai * r.vim;
-        out.y += ar * r.vim + ai * r.vre;
-        vis[k] = out;
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int ps = 0; ps < kPasses; ++ps) {
+            const int pair = lane + 32 * ps;
+            if (pair >= W * W) break;
+            const int a = pair % W, b = pair / W;
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                const float wc = wt[2 * W + c];
+                sr = fmaf(wc, f[ps][c].x, sr);
+                si = fmaf(wc, f[ps][c].y, si);
+            }
+            const float wab = wt[a] * wt[W + b];
+            ar = fmaf(wab, sr, ar);
+            ai = fmaf(wab, si, ai);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ar += __shfl_xor_sync(0xffffffffu, ar, o);
+            ai += __shfl_xor_sync(0xffffffffu, ai, o);
+        }
+        if (lane == 0) {
+            float2 out = vis[k];
+            out.x += ar * r.vre - ai * r.vim;
+            out.y += ar * r.vim + ai * r.vre;
+            vis[k] = out;
+        }
     }
 }
 
@@ -566,12 +573,23 @@ cudaError_t launch_unfold(const ws_plan_s *p, const double *uvw, int64_t M, floa
 cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64_t M, float2 *vis,
                                 cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    const dim3 grid(blocks_for(M * 32, kDegridThreads));
+    // resident CTAs only (the kernel loops over the visibilities), at most one warp per visibility
+    const int64_t want = blocks_for(M * 32, kDegridThreads);
+    auto resident = [&](auto kernel, int w) {
+        static int per_sm[kMaxW + 1] = {};
+        if (per_sm[w] == 0) {
+            int b = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kDegridThreads, 0) != cudaSuccess || b < 1)
+                b = 1;
+            per_sm[w] = b;
+        }
+        return (unsigned)std::min<int64_t>(want, (int64_t)p->sms * per_sm[w]);
+    };
 #define WS_DEGRID_CASE(w)                                                                                     \
     case w:                                                                                                  \
-        degrid3d_kernel<w><<<grid, kDegridThreads, 0, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_list,    \
-                                                           p->d_offsets + p->ntiles, p->d_stack,               \
-                                                           chunk * p->P, planes, vis);                         \
+        degrid3d_kernel<w><<<resident(degrid3d_kernel<w>, w), kDegridThreads, 0, s>>>(                       \
+            p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_list, p->d_offsets + p->ntiles, p->d_stack, chunk * p->P, \
+            planes, vis);                                                                                    \
         break;
     switch (p->L.W) {
         WS_DEGRID_CASE(1)
