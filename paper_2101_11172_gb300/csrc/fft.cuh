@@ -186,6 +186,25 @@ template <>
 __device__ __forceinline__ void dft<7>(float2 *v, bool inv, const float2 *__restrict__, int) {
     dft_odd<7>(v, inv);
 }
+// 10 = 2 x 5: five-point DFTs of the even and of the odd inputs, then
+// X_k = E_k + w10^k O_k and X_{k+5} = E_k - w10^k O_k, w10 = exp(-+ 2 pi i / 10).
+template <>
+__device__ __forceinline__ void dft<10>(float2 *v, bool inv, const float2 *__restrict__, int) {
+    float2 e[5] = {v[0], v[2], v[4], v[6], v[8]}, o[5] = {v[1], v[3], v[5], v[7], v[9]};
+    dft_odd<5>(e, inv);
+    dft_odd<5>(o, inv);
+    // cos and sin of 2 pi k / 10, k = 1..4 (cos(pi/5) = (sqrt 5 + 1) / 4, cos(2 pi/5) = (sqrt 5 - 1) / 4)
+    constexpr float c[5] = {1.f, 0.80901699437494742f, 0.30901699437494742f, -0.30901699437494742f,
+                            -0.80901699437494742f};
+    constexpr float sn[5] = {0.f, 0.58778525229247313f, 0.95105651629515357f, 0.95105651629515357f,
+                             0.58778525229247313f};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float2 t = k == 0 ? o[0] : cmul(o[k], make_float2(c[k], inv ? sn[k] : -sn[k]));
+        v[k] = cadd(e[k], t);
+        v[k + 5] = csub(e[k], t);
+    }
+}
 
 // v[m] *= w^m for m = 1..R-1, w = exp(-+ 2 pi i e / n).  The table holds w^m
 // to half an ulp, but a warp's loads of w^m for m > 1 scatter over many
@@ -221,6 +240,19 @@ template <int R>
 __device__ __forceinline__ void twiddle_all(float2 *v, const float2 *__restrict__ tw, int e, bool inv) {
     if constexpr (R == 16 || R == 8) {
         twiddle_powers<R>(v, twiddle(tw, e, inv), twiddle(tw, 4 * e, inv));
+    } else if constexpr (R == 10) {
+        // w^m from w and w^4, products at most two deep
+        const float2 w1 = twiddle(tw, e, inv), w4 = twiddle(tw, 4 * e, inv);
+        const float2 w2 = cmul(w1, w1), w3 = cmul(w2, w1), w8 = cmul(w4, w4);
+        v[1] = cmul(v[1], w1);
+        v[2] = cmul(v[2], w2);
+        v[3] = cmul(v[3], w3);
+        v[4] = cmul(v[4], w4);
+        v[5] = cmul(v[5], cmul(w4, w1));
+        v[6] = cmul(v[6], cmul(w4, w2));
+        v[7] = cmul(v[7], cmul(w4, w3));
+        v[8] = cmul(v[8], w8);
+        v[9] = cmul(v[9], cmul(w8, w1));
     } else {
         // R <= 7: w^m from w by products, at most three roundings deep
         static_assert(R <= 7, "radices 3 to 7");
@@ -341,7 +373,8 @@ __device__ __forceinline__ void fft_many(float2 *buf, const FftPlan &P, const fl
         case 4: fftdev::dit_first<4, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store); break;
         default:
             if constexpr (MIXED) {
-                if (P.radix[0] == 7) fftdev::dit_first<7, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
+                if (P.radix[0] == 10) fftdev::dit_first<10, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
+                else if (P.radix[0] == 7) fftdev::dit_first<7, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
                 else if (P.radix[0] == 5) fftdev::dit_first<5, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
                 else fftdev::dit_first<3, COUNT, POW2>(buf, P, tw, inv, tid, nthr, load, store);
             }
@@ -357,7 +390,9 @@ __device__ __forceinline__ void fft_many(float2 *buf, const FftPlan &P, const fl
             case 4: fftdev::dit_stage<4, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store); break;
             default:
                 if constexpr (MIXED) {
-                    if (R == 7)
+                    if (R == 10)
+                        fftdev::dit_stage<10, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store);
+                    else if (R == 7)
                         fftdev::dit_stage<7, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store);
                     else if (R == 5)
                         fftdev::dit_stage<5, COUNT, POW2>(buf, P, L, P.L_mul[s], last, tw, inv, tid, nthr, store);

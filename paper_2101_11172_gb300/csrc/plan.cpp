@@ -150,17 +150,33 @@ bool fft_make_plan(int n, FftPlan *F) {
         m /= 2;
         ++a;
     }
+    // the power-of-two radices for 2^a (none for radix 2: a = 1 is not possible)
+    auto pow2_radix = [](int a) { return (a >= 8 || a == 4 || a == 7) ? 16 : (a == 3 || a == 5 || a == 6) ? 8 : 4; };
+    auto pow2_stages = [&](int a) {
+        int s = 0;
+        for (; a > 0; ++s) {
+            if (a == 1) return 99;
+            const int r = pow2_radix(a);
+            a -= r == 16 ? 4 : (r == 8 ? 3 : 2);
+        }
+        return s;
+    };
+    // one factor 2 and one factor 5 make a radix-10 stage where that saves a stage
+    // (N' = 5600 = 2^5 5^2 7: 16, 10, 7, 5 instead of 8, 4, 7, 5, 5)
+    const bool ten = m % 5 == 0 && a >= 1 && pow2_stages(a - 1) < pow2_stages(a);
+    if (ten) {
+        --a;
+        m /= 5;
+    }
     int ns = 0;
     while (a > 0) {
-        int r;
-        if (a >= 8 || a == 4 || a == 7) r = 16;
-        else if (a == 3 || a == 5 || a == 6) r = 8;
-        else if (a == 2) r = 4;
-        else return false;
+        if (a == 1) return false;
+        const int r = pow2_radix(a);
         F->radix[ns++] = r;
         a -= r == 16 ? 4 : (r == 8 ? 3 : 2);
         if (ns >= 8) return false;
     }
+    if (ten) F->radix[ns++] = 10;
     for (int p : {7, 5, 3})
         while (m % p == 0) {
             if (ns >= 8) return false;

@@ -77,6 +77,13 @@ def test_nonstandard_grid_and_x0(dev):
     assert g.Np == 384
 
 
+def test_radix_ten_plan(dev):
+    # N' = 160 = 2^5 5: the runtime plan pairs one 2 with the 5 (radices 16, 10)
+    c = case(N=80, M=1500, W=7, seed=17)
+    v, d, g, *_ = check_against_oracle(c, dev)
+    assert g.Np == 160
+
+
 def test_no_z_offset_variant(dev):
     from paper_2101_11172_gb300 import WS_FLAG_NO_Z_OFFSET
     check_against_oracle(case(seed=11), dev, flags=WS_FLAG_NO_Z_OFFSET, z_offset=False)
