@@ -179,16 +179,43 @@ def stage_bytes(stage: str, N: int, Np: int, Nw: int, total_planes: int, M: int,
     return None
 
 
+def _code_tokens(text: str) -> str:
+    """C/C++/CUDA source with comments removed and whitespace runs collapsed (string
+    and character literals kept as they are), so that editing a comment leaves the
+    hash of the code unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def library_source_sha() -> str:
     """Hash of the library's device code (the kernels, and the headers that shape their
-    arguments): any change there invalidates the DRAM counters of profiles/traffic.json.
-    Host-only files (plan construction, batches, the least-misfit fit) are left out."""
+    arguments), comments and layout aside: any change to the code invalidates the DRAM
+    counters of profiles/traffic.json.  Host-only files (plan construction, batches,
+    the least-misfit fit) are left out."""
     import glob
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_2101_11172_gb300", "csrc", "*"))):
         if f.endswith((".cu", ".cuh")) or os.path.basename(f) in ("ws_internal.hpp", "fft_plan.hpp"):
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+            with open(f, encoding="utf-8") as fh:
+                h.update(_code_tokens(fh.read()).encode())
     return h.hexdigest()
 
 

@@ -45,8 +45,9 @@ EncodeTiled encode_tiled() {
 // Element (S, R) of plane p sits at float offset 2 (((R / 4) N' + S) 4 + R % 4)
 // + 2 N'^2 p: dimension 0 runs over the 8 floats of a block row, 1 over the
 // N' rows S (32 bytes apart), 2 over the N'/4 column blocks (32 N' bytes
-// apart), 3 over the P planes.  A box {8, 1, 4, 1} is one strip of TU = 16
-// columns of one row, 128 contiguous bytes in shared memory in column order.
+// apart), 3 over the P planes.  A box {8, 1, B, 1}, B = min(256, N'/4), is B
+// column blocks of one row: 4B consecutive columns, 32B contiguous bytes in
+// shared memory in column order.
 cudaError_t row_tensor_map(const ws_plan_s *p, CUtensorMap *map) {
     const EncodeTiled encode = encode_tiled();
     if (!encode) return cudaErrorNotSupported;

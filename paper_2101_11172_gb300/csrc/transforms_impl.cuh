@@ -445,7 +445,7 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 }
 
 // The stack as a 4-D FP32 tensor for TMA row copies: {8 floats of a column
-// block's row, N' rows, N'/4 blocks, P planes}, boxes of one strip.
+// block's row, N' rows, N'/4 blocks, P planes}, boxes of min(256, N'/4) blocks of one row.
 cudaError_t row_tensor_map(const ws_plan_s *p, CUtensorMap *map);
 
 // Launchers of one FFT variant.
