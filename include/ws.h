@@ -91,6 +91,13 @@ typedef struct {
     int64_t kernel_launches;           /* kernel launches of the counted calls */
     double stage_ms[WS_NSTAGES];       /* device time per stage (WS_FLAG_TIMING plans only) */
     int64_t stage_launches[WS_NSTAGES];/* kernel launches per stage */
+    double stage_bytes[WS_NSTAGES];    /* occupied algorithmic bytes per stage (WS_FLAG_TIMING plans,
+                                          calls that wait for their stream): the bytes each stage must
+                                          move for the w-stack tiles and column strips that some
+                                          visibility footprint touches (every other stack cell is zero
+                                          in gridding and never read in degridding), plus its inputs
+                                          and outputs; 0 for the binning stage */
+    int64_t waits_timed_out;           /* bounded device waits that gave up (WS_ERR_TIMEOUT calls) */
 } ws_stats_t;
 
 typedef struct {
@@ -150,8 +157,13 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
 /* Algorithm 5: vis (device complex64 M, read) at uvw (device double M x 3) ->
  * dirty (device complex64 N x N, overwritten).  Out-of-range visibilities are
  * skipped and counted as for ws_degrid.  The row transforms of N' = 512 ..
- * 4096 wait for their TMA row copies with a bounded wait; a wait that gives up
- * leaves dirty incomplete and the call returns WS_ERR_TIMEOUT. */
+ * 4096 wait for their TMA row copies with a bounded wait (2^20 polls); a wait
+ * that gives up leaves dirty incomplete, is counted in ws_stats_t
+ * waits_timed_out, and the call returns WS_ERR_TIMEOUT.  The environment
+ * variable WS_WAIT_POLLS, read at every call, sets the poll limit of the
+ * first wait for each plane's row (0 gives up at once; the wait that drains
+ * a copy in flight before the CTA returns keeps the full limit), so that the
+ * timeout path can be exercised without any fault. */
 ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
                   void *dirty, ws_stream_t stream);
 

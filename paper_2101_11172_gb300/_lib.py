@@ -38,12 +38,16 @@ class PlanInfo(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("calls", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("stage_ms", ctypes.c_double * len(STAGES)),
-                ("stage_launches", ctypes.c_int64 * len(STAGES))]
+                ("stage_launches", ctypes.c_int64 * len(STAGES)),
+                ("stage_bytes", ctypes.c_double * len(STAGES)),
+                ("waits_timed_out", ctypes.c_int64)]
 
     def as_dict(self):
         return {"calls": self.calls, "kernel_launches": self.kernel_launches,
                 "stage_ms": {n: self.stage_ms[i] for i, n in enumerate(STAGES)},
-                "stage_launches": {n: self.stage_launches[i] for i, n in enumerate(STAGES)}}
+                "stage_launches": {n: self.stage_launches[i] for i, n in enumerate(STAGES)},
+                "stage_bytes": {n: self.stage_bytes[i] for i, n in enumerate(STAGES)},
+                "waits_timed_out": self.waits_timed_out}
 
 
 class Instance(ctypes.Structure):

@@ -51,6 +51,7 @@ struct ws_batch_s {
     cudaStream_t origin = nullptr;     // capture stream
     cudaStream_t br[kMaxBranches] = {};
     cudaEvent_t fork = nullptr, join[kMaxBranches] = {};
+    cudaEvent_t ready = nullptr, tuned = nullptr;   // order the tuning runs after, and before, the caller's stream
     Graph graph[2];                    // 0 = grid, 1 = degrid
 };
 
@@ -77,6 +78,8 @@ void release_batch(ws_batch_s *b) {
         if (b->join[k]) cudaEventDestroy(b->join[k]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ready) cudaEventDestroy(b->ready);
+    if (b->tuned) cudaEventDestroy(b->tuned);
     if (b->origin) cudaStreamDestroy(b->origin);
     delete b;
 }
@@ -212,10 +215,20 @@ ws_status run(ws_batch_s *b, int dir, const std::vector<const void *> &ptr, cuda
     if (!g.exec || g.key != ptr) {
         destroy_graph(g);
         if (b->K == 0) {
-            // the first call decides K; the other direction's graph must then be recaptured
+            // the first call decides K; the other direction's graph must then be recaptured.
+            // The timing runs execute on the batch's own stream: they start after the
+            // work already queued on the caller's stream (which may still be producing
+            // this call's inputs, or using memory the outputs now occupy) and the
+            // caller's stream waits for them in turn.
             destroy_graph(b->graph[1 - dir]);
+            cudaError_t e = cudaEventRecord(b->ready, stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ready, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "ws_batch: ordering the tuning runs");
             ws_status st = tune(b, dir, ptr, g);
+            e = cudaEventRecord(b->tuned, b->origin);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, b->tuned, 0);
             if (st != WS_OK) return st;
+            if (e != cudaSuccess) return cuda_fail(e, "ws_batch: ordering the tuning runs");
         } else {
             ws_status st = capture(b, dir, ptr, &g.exec);
             if (st != WS_OK) return st;
@@ -322,6 +335,8 @@ ws_status ws_batch_create(ws_batch_t *out, int32_t n, const ws_instance_t *inst,
     if (st == WS_OK) {
         e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->tuned, cudaEventDisableTiming);
         for (int k = 0; k < kMaxBranches && e == cudaSuccess; ++k) {
             e = cudaStreamCreateWithFlags(&b->br[k], cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);

@@ -52,7 +52,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const double *uvw, int64_t M, void *vis,
                                        ws_stream_t stream) {
     using namespace ws;
-    if (!plan || M < 0 || !image || (M > 0 && (!uvw || !vis))) {
+    if (!plan || M < 0 || !image || (M > 0 && (!uvw || !vis)) || M > kMaxVis) {
         set_error("ws_degrid_noalloc: invalid argument");
         return WS_ERR_ARG;
     }

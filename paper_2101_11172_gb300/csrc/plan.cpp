@@ -88,7 +88,9 @@ void release(ws_plan_s *p) {
     cudaFree(p->d_col_occ);
     cudaFree(p->d_img);
     cudaFree(p->d_drop);
+    cudaFree(p->d_occ_counts);
     if (p->h_drop) cudaFreeHost(p->h_drop);
+    if (p->h_occ_counts) cudaFreeHost(p->h_occ_counts);
     delete p;
 }
 
@@ -214,7 +216,57 @@ bool fft_make_plan(int n, FftPlan *F) {
     return true;
 }
 
-ws_status finish_call(ws_plan_s *p, cudaStream_t s) {
+// Occupied algorithmic bytes of one call per stage, from the occupancy counts
+// the call copied to h_occ_counts.  Per plane, a column pass reads or writes
+// the occupied tiles (TV x TU cells each) and the N crop rows of every
+// occupied (t-tile, u-strip) strip; a row pass the N rows of the occupied
+// strips; gridding writes whole occupied tiles (TT planes) and reads one
+// record and one list entry per (visibility, tile) pair; degridding gathers
+// from the occupied tiles and reads and writes its output once per chunk.
+void add_occupied_bytes(ws_plan_s *p, bool grid, int64_t M) {
+    const Launch &L = p->L;
+    const double tile_plane = (double)TV * TU * sizeof(float2), strip_plane = (double)L.N * TU * sizeof(float2);
+    double t_valid = 0.0, s_valid = 0.0, t_full = 0.0;
+    for (int tt = 0; tt < L.ntt; ++tt) {
+        const double valid = std::min(TT, L.Nw - tt * TT);
+        t_valid += valid * p->h_occ_counts[2 * tt];
+        s_valid += valid * p->h_occ_counts[2 * tt + 1];
+        t_full += (double)TT * p->h_occ_counts[2 * tt];
+    }
+    const double entries = p->h_occ_counts[2 * L.ntt];
+    const double img = (double)L.N * L.N;
+    const int nchunks = (L.ntt * TT + p->P - 1) / p->P;
+    double *b = p->stats.stage_bytes;
+    if (grid) {
+        b[WS_STAGE_PREP] += (double)M * (24 + 8 + sizeof(VisRec));
+        b[WS_STAGE_GRID3D] += t_full * tile_plane + entries * (sizeof(uint32_t) + sizeof(VisRec));
+        b[WS_STAGE_COLS_INV] += t_valid * tile_plane + s_valid * strip_plane;
+        b[WS_STAGE_ROWS_INV] += s_valid * strip_plane + img * (sizeof(float2) + sizeof(float) + sizeof(float2)) +
+                                (nchunks - 1) * img * 2 * sizeof(float4);
+    } else {
+        b[WS_STAGE_PREP] += (double)M * (24 + sizeof(VisRec));
+        b[WS_STAGE_CORRECT] += img * (sizeof(float2) + sizeof(float) + sizeof(float2));
+        b[WS_STAGE_ROWS_FWD] += nchunks * img * 2 * sizeof(float2) + s_valid * strip_plane;
+        b[WS_STAGE_COLS_FWD] += s_valid * strip_plane + t_valid * tile_plane;
+        b[WS_STAGE_DEGRID3D] += t_valid * tile_plane + entries * (sizeof(uint32_t) + sizeof(VisRec)) +
+                                nchunks * (double)M * 2 * sizeof(float2);
+    }
+}
+
+// Statistics only: occupancy counts of this call to the host (WS_FLAG_TIMING).
+cudaError_t copy_occ_counts(ws_plan_s *p, cudaStream_t s) {
+    if (!(p->flags & WS_FLAG_TIMING)) return cudaSuccess;
+    cudaError_t e = launch_occ_count(p, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->h_occ_counts, p->d_occ_counts, (size_t)2 * p->L.ntt * sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->h_occ_counts + 2 * p->L.ntt, p->d_offsets + p->ntiles, sizeof(uint32_t),
+                            cudaMemcpyDeviceToHost, s);
+    return e;
+}
+
+ws_status finish_call(ws_plan_s *p, cudaStream_t s, bool grid, int64_t M) {
     cudaError_t e = cudaMemcpyAsync(p->h_drop, p->d_drop, kCounters * sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "reading the drop counters");
@@ -222,6 +274,8 @@ ws_status finish_call(ws_plan_s *p, cudaStream_t s) {
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "waiting for the stream");
     p->last_dropped = (int64_t)(p->h_drop[0] + p->h_drop[1]);
+    p->stats.waits_timed_out += (int64_t)p->h_drop[2];
+    if ((p->flags & WS_FLAG_TIMING) && M > 0) add_occupied_bytes(p, grid, M);
     if (p->h_drop[2]) {
         set_error(std::to_string(p->h_drop[2]) + " device waits for copies gave up; the output is incomplete");
         return WS_ERR_TIMEOUT;
@@ -539,6 +593,12 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     WS_TRY(dev_alloc(&p->d_drop, (size_t)kCounters, &p->bytes), "allocating drop counters");
     WS_TRY(cudaMallocHost((void **)&p->h_drop, kCounters * sizeof(unsigned long long)), "allocating pinned counters");
     std::memset(p->h_drop, 0, kCounters * sizeof(unsigned long long));
+    if (flags & WS_FLAG_TIMING) {
+        WS_TRY(dev_alloc(&p->d_occ_counts, (size_t)2 * L.ntt, &p->bytes), "allocating occupancy counts");
+        WS_TRY(cudaMallocHost((void **)&p->h_occ_counts, ((size_t)2 * L.ntt + 1) * sizeof(uint32_t)),
+               "allocating pinned occupancy counts");
+        std::memset(p->h_occ_counts, 0, ((size_t)2 * L.ntt + 1) * sizeof(uint32_t));
+    }
 #undef WS_TRY
     *out = p;
     return WS_OK;
@@ -558,9 +618,16 @@ ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64
         if ((e = launch_prep(p, uvw, vis, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: prep kernel");
     }
     {
-        StageTimer t(p, s, WS_STAGE_BIN, M > 0 ? 6 : 3);
+        StageTimer t(p, s, WS_STAGE_BIN, (M > 0 ? 6 : 3) + ((p->flags & WS_FLAG_TIMING) ? 1 : 0));
         if ((e = launch_bin(p, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: binning kernels");
         if ((e = launch_mark_grid(p, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy kernel");
+    }
+    if ((e = copy_occ_counts(p, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy statistics");
+    // test knob: the poll limit of inv_rows' first wait for each plane's row copy
+    p->wait_polls = kWaitPolls;
+    if (const char *env = std::getenv("WS_WAIT_POLLS")) {
+        const long v = std::strtol(env, nullptr, 10);
+        if (v >= 0 && v < kWaitPolls) p->wait_polls = (int)v;
     }
     const int total = p->L.ntt * TT;
     const int nchunks = (total + p->P - 1) / p->P;
@@ -599,10 +666,11 @@ ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, i
             return cuda_fail(e, "ws_degrid: prep kernel");
     }
     {
-        StageTimer t(p, s, WS_STAGE_BIN, 7);
+        StageTimer t(p, s, WS_STAGE_BIN, 7 + ((p->flags & WS_FLAG_TIMING) ? 1 : 0));
         if ((e = launch_bin(p, M, false, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: binning kernels");
         if ((e = launch_mark(p, M, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy kernel");
     }
+    if ((e = copy_occ_counts(p, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy statistics");
     {
         StageTimer t(p, s, WS_STAGE_CORRECT, 1);
         if ((e = launch_correct_image(p, image, s)) != cudaSuccess)
@@ -654,7 +722,7 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
     if (st != WS_OK) return st;
     st = enqueue_grid(p, uvw, static_cast<const float2 *>(vis), M, static_cast<float2 *>(dirty), s);
     if (st != WS_OK) return st;
-    return finish_call(p, s);
+    return finish_call(p, s, true, M);
 }
 
 ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_t M, void *vis,
@@ -674,7 +742,7 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
     if (st != WS_OK) return st;
     st = enqueue_degrid(p, static_cast<const float2 *>(image), uvw, M, static_cast<float2 *>(vis), s);
     if (st != WS_OK) return st;
-    return finish_call(p, s);
+    return finish_call(p, s, false, M);
 }
 
 ws_status ws_plan_dropped(ws_plan_t plan, int64_t *dropped) {

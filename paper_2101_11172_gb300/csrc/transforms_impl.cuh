@@ -217,11 +217,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
         : "memory");
     return done != 0;
 }
-// Wait for the phase of the given parity to complete, giving up after about
-// 2^20 polls (a few hundred milliseconds): false if it did not complete.
-constexpr int kWaitPolls = 1 << 20;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-    for (int i = 0; i < kWaitPolls; ++i) {
+// Wait for the phase of the given parity to complete, giving up after
+// `polls` polls (kWaitPolls: a few hundred milliseconds): false if it did not
+// complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int polls = kWaitPolls) {
+    for (int i = 0; i < polls; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         __nanosleep(64);
     }
@@ -261,7 +261,7 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 const __grid_constant__ CUtensorMap row_map, const uint8_t *__restrict__ col_occ, int plane0,
                 int planes, const float2 *__restrict__ zsplit, const float *__restrict__ corr,
                 float4 *__restrict__ acc, int first, int last, float2 *__restrict__ dirty,
-                unsigned long long *__restrict__ timeouts) {
+                unsigned long long *__restrict__ timeouts, int wait_polls) {
     extern __shared__ __align__(16) float2 sbuf[];
     const int Np = L.Np, N = L.N, half = N / 2;
     const int ii = blockIdx.x;
@@ -319,11 +319,11 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 }
                 live_tt = tt;
             }
-            const bool ok = mbar_wait(&bar[p & 1], (p >> 1) & 1);
+            const bool ok = mbar_wait(&bar[p & 1], (p >> 1) & 1, wait_polls);
             if (__syncthreads_or(!ok)) {     // uniform: give up on this row
                 if (tid == 0) {
                     atomicAdd(timeouts, 1ull);
-                    mbar_wait(&bar[p & 1], (p >> 1) & 1);
+                    mbar_wait(&bar[p & 1], (p >> 1) & 1);   // drain the copy in flight (full limit)
                 }
                 __syncthreads();
                 return;
@@ -491,7 +491,7 @@ struct Transforms {
         }
         inv_rows_kernel<NP><<<p->L.N, kRowThreads, smem_inv_rows<NP>(p->fft, p->L.N), s>>>(
             p->L, p->fft, p->d_tw, p->d_stack, map, p->d_col_occ, chunk * p->P, planes, p->d_zsplit, p->d_corr,
-            p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty, p->d_drop + 2);
+            p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty, p->d_drop + 2, p->wait_polls);
         return cudaGetLastError();
     }
 };

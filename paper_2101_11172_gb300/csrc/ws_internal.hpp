@@ -24,6 +24,8 @@ constexpr int kMaxDeg = 16;
 // Per-call device counters: visibilities dropped for non-finite u, v; for w
 // outside the plan's range; and bounded device waits that gave up.
 constexpr int kCounters = 3;
+// Polls of a bounded mbarrier wait (a few hundred milliseconds) before it gives up.
+constexpr int kWaitPolls = 1 << 20;
 
 // One visibility after pre-processing: first grid point of its W x W x W
 // footprint (u and v wrapped into [0, N'), t relative to the plan's t_lo;
@@ -87,6 +89,11 @@ struct ws_plan_s {
     float2 *d_img = nullptr;       // N x N: corrected image (degridding)
     unsigned long long *d_drop = nullptr;   // kCounters: [0] non-finite uv, [1] w out of range, [2] timed-out waits
     unsigned long long *h_drop = nullptr;   // pinned mirror
+    int wait_polls = ws::kWaitPolls;        // limit of inv_rows' first wait per plane (WS_WAIT_POLLS)
+    // occupancy statistics (WS_FLAG_TIMING): per t-tile, occupied tiles and
+    // (t-tile, u-strip) strips, then the number of tile-list entries
+    uint32_t *d_occ_counts = nullptr;       // 2 ntt
+    uint32_t *h_occ_counts = nullptr;       // pinned: 2 ntt + 1
     int64_t last_dropped = 0;
     int64_t bytes = 0;
     // statistics (WS_FLAG_TIMING adds CUDA events around each stage)
@@ -123,6 +130,7 @@ cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
 cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s);
 cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s);
+cudaError_t launch_occ_count(const ws_plan_s *p, cudaStream_t s);
 cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s);
 cudaError_t launch_unfold(const ws_plan_s *p, const double *uvw, int64_t M, float2 *vis, cudaStream_t s);

@@ -169,6 +169,25 @@ __global__ void occ_kernel(Launch L, const uint32_t *__restrict__ per_tile, int6
     }
 }
 
+// Statistics only (WS_FLAG_TIMING): occupied tiles and occupied (t-tile,
+// u-strip) strips of one t-tile per CTA.
+__global__ void occ_count_kernel(Launch L, const uint8_t *__restrict__ tile_occ, const uint8_t *__restrict__ col_occ,
+                                 uint32_t *__restrict__ counts) {
+    const int tt = blockIdx.x;
+    const int64_t per = (int64_t)L.ntu * L.ntv;
+    uint32_t tiles = 0, strips = 0;
+    for (int64_t i = threadIdx.x; i < per; i += blockDim.x) tiles += tile_occ[tt * per + i];
+    for (int i = threadIdx.x; i < L.ntu; i += blockDim.x) strips += col_occ[(int64_t)tt * L.ntu + i];
+    for (int o = 16; o > 0; o >>= 1) {
+        tiles += __shfl_xor_sync(0xffffffffu, tiles, o);
+        strips += __shfl_xor_sync(0xffffffffu, strips, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&counts[2 * tt], tiles);
+        atomicAdd(&counts[2 * tt + 1], strips);
+    }
+}
+
 // Exclusive scan of n uint32 (n <= 4096 * 4096): per-block scan of 4096
 // elements, scan of the block sums in one block, then add back.
 constexpr int kScanThreads = 1024;
@@ -524,6 +543,13 @@ cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     occ_kernel<false><<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_offsets, p->ntiles, p->d_tile_occ,
                                                                  p->d_col_occ);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_occ_count(const ws_plan_s *p, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p->d_occ_counts, 0, (size_t)2 * p->L.ntt * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    occ_count_kernel<<<p->L.ntt, 256, 0, s>>>(p->L, p->d_tile_occ, p->d_col_occ, p->d_occ_counts);
     return cudaGetLastError();
 }
 

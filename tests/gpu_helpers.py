@@ -19,6 +19,31 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
 
 
+# Element-wise bar, in units of the reference's RMS: FP32 rounding spreads a
+# near-Gaussian error of roughly equal size over every output, so |error| is
+# close to Rayleigh distributed and its largest value over n outputs sits near
+# sqrt(2 ln n) times its RMS -- 5.7 for n = 1e7, the largest count compared.
+# With the RMS error allowed up to tol, no single output may be off by more
+# than K_ELEM tol rms(ref).  A faint region that is wrong by more than that
+# fails, however small the region.
+K_ELEM = 6.0
+
+
+def worst_element(a, ref):
+    """(index, |a - ref| / rms(ref)) of the output farthest from the reference."""
+    a, ref = np.asarray(a).ravel(), np.asarray(ref).ravel()
+    err = np.abs(a - ref)
+    i = int(np.argmax(err))
+    return i, float(err[i] / np.sqrt(np.mean(np.abs(ref) ** 2)))
+
+
+def assert_elementwise(a, ref, tol, what):
+    """Every output within K_ELEM x tol x rms(ref) of the reference (prints the worst)."""
+    i, e = worst_element(a, ref)
+    print(f"{what}: worst element {i}: |error| = {e:.2e} rms(ref) (bar {K_ELEM * tol:.2e})")
+    assert e <= K_ELEM * tol, (what, i, e, K_ELEM * tol)
+
+
 def tol_for(W, x0):
     """Relative-RMS bar: 2e-6, or the method's own sqrt(3) E when that is larger."""
     return max(REL_TOL, 1.5 * math.sqrt(3) * least_misfit(W, x0).E)

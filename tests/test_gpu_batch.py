@@ -112,6 +112,35 @@ def test_batch_replays_recaptures_and_branch_counts_agree(dev):
         assert rel(a, c) < 1e-6
 
 
+def test_batch_tuning_waits_for_the_callers_stream(dev):
+    # The first call of a batch made with branches = 0 times candidate graphs on the
+    # batch's own stream.  Those runs must start only after the work already queued on
+    # the caller's stream (here: a long kernel, then a read of the output buffers' old
+    # contents, then the copies that produce the inputs), and the caller's stream must
+    # wait for them before it goes on.
+    from paper_2101_11172_gb300.batch import Batch
+    wls = small_batch(4)
+    uvw, img, vis = to_dev(wls, dev)
+    with Batch(instances(wls), 0.25, 7, branches=1, device=dev) as b1:
+        want = as_np(b1.degrid(img, uvw))
+    with Batch(instances(wls), 0.25, 7, device=dev) as b:
+        assert b.branches == 0
+        out = [torch.full((w.M,), 7.0, dtype=torch.complex64, device=dev) for w in wls]
+        late = [torch.full_like(u, float("nan")) for u in uvw]
+        torch.cuda.synchronize()
+        torch.cuda._sleep(int(2e9))                 # about a second of work on the caller's stream
+        seen = [o.clone() for o in out]             # queued behind it: the outputs' old contents
+        for a, u in zip(late, uvw):
+            a.copy_(u)                              # the inputs only now become valid
+        got = b.degrid(img, late, out=out)
+        torch.cuda.synchronize()
+        assert b.last_status == 0 and b.branches in (1, 2, 4)
+        for s_ in seen:
+            assert bool(torch.all(s_ == 7.0)), "a tuning run wrote an output before the caller's stream read it"
+        for a, c in zip(as_np(got), want):
+            assert rel(a, c) < 1e-6
+
+
 def test_batch_reports_the_instance_that_dropped(dev):
     from paper_2101_11172_gb300 import _lib
     from paper_2101_11172_gb300.batch import Batch
