@@ -167,6 +167,24 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
 ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
                   void *dirty, ws_stream_t stream);
 
+/* Bind a visibility coordinate set to the plan.  The tap rule of Section 3.3,
+ * the offsets nu, the pre-phase exp(2 pi i w (n0 - 1)) and the sort of the
+ * visibilities into gridding tiles depend on uvw alone, so a consumer that
+ * calls ws_grid and ws_degrid many times on the same uvw (conjugate
+ * gradients, autograd, any iterative imager) can have them made once.  This
+ * call makes them for both directions, with the occupancy of the w-stack,
+ * into plan-owned buffers (allocated on first use, grown as needed).  Later
+ * ws_grid / ws_degrid calls whose uvw pointer and M equal the bound ones skip
+ * that work and give the same results as unbound calls.  Calls with any other
+ * uvw or M run unbound, as before.
+ *   uvw  device double M x 3, or NULL to unbind (the buffers are kept)
+ * The caller must keep the bound array allocated and unchanged until it binds
+ * another set or unbinds: the plan does not see later changes to its contents.
+ * Visibilities the bound set drops (non-finite u, v; w outside the plan's
+ * range) are reported by every later call on it, as for an unbound call.
+ * Waits for the stream before it returns. */
+ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stream_t stream);
+
 /* Allocation-free degridding.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory while they run (a
  * process whose device memory budget is fixed at start-up, a plug-in whose

@@ -11,9 +11,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
   improved one (Eq. N_{w'}+W, with and without z offset) for a baseline set.
 
 ``python -m oracle.explore`` prints all three for the default grids.  The
-fit is the oracle's Gauss-Newton of ``lmfit``: at W = 12 with x0 >= 0.4 it
-stops far above the optimum (E = 1.4e-5), a limit of the FP64 normal
-equations there, not of the method.
+fit is the oracle's ``lmfit.least_misfit``; E falls with W at every x0 of the
+table up to W = 14.
 """
 from __future__ import annotations
 
@@ -23,7 +22,7 @@ from .geometry import layers_improved, layers_original
 from .lmfit import error_bound, least_misfit, tophat_h, tophat_weights
 
 
-def error_table(Ws=range(1, 13), x0s=(0.1, 0.15, 0.2, 0.25, 0.3, 0.35, 0.4)):
+def error_table(Ws=range(1, 15), x0s=(0.1, 0.15, 0.2, 0.25, 0.3, 0.35, 0.4)):
     """{(W, x0): E} for the least-misfit C and h of each pair (Section 3.3)."""
     return {(W, x0): least_misfit(W, x0).E for W in Ws for x0 in x0s}
 
@@ -42,9 +41,9 @@ def layers(dn: float, dw: float, z0: float = 0.25, W: int = 7):
 
 def main():
     x0s = (0.1, 0.15, 0.2, 0.25, 0.3, 0.35, 0.4)
-    tab = error_table(range(1, 13), x0s)
+    tab = error_table(range(1, 15), x0s)
     print("E(W, x0)   " + "  ".join(f"x0={x0:<6}" for x0 in x0s))
-    for W in range(1, 13):
+    for W in range(1, 15):
         print(f"W = {W:2d}    " + "  ".join(f"{tab[(W, x0)]:9.2e}" for x0 in x0s))
     print("\ntop hat: z0, E, sqrt(pi/3) z0")
     for z0, e, approx in tophat_curve():

@@ -32,10 +32,15 @@ How this module computes the minimiser (the paper gives no algorithm):
   coefficients alone, and its small residual makes Gauss-Newton converge in a
   handful of iterations.  (Plain alternation between the two partial
   minimisations converges to the same point but needs thousands of sweeps.)
+  A Levenberg-Marquardt step replaces a Gauss-Newton step that fails to lower
+  E, and for large x0 the minimiser is followed up from x0 = 1/4 (see
+  ``least_misfit``).
 
 Pins (tests/test_oracle_lmfit.py): E(W=7, x0=0.25) against the quoted
 1.3e-7 (Section 6); the layer multipliers 6, 27, 500 quoted for Figure 3; the
-top-hat closed form of Section 6; evenness; W=1 against the top hat.
+top-hat closed form of Section 6; evenness; W=1 against the top hat; E
+falling with W at every x0 up to 0.45 and W up to 14, and reaching FP64
+rounding level at W = 14, x0 = 1/4 (Section 6.3: double precision at W = 14).
 """
 from __future__ import annotations
 
@@ -201,17 +206,20 @@ def _expand(cols, vec, W, D):
     return beta
 
 
-@lru_cache(maxsize=64)
-def least_misfit(W: int, x0: float, degree: int = 20, nx: int = 64,
-                 n_nu: int = 64, max_iter: int = 60) -> LeastMisfit:
-    """Minimise E over even C (support W) and real h for cropping parameter x0."""
-    if not (1 <= W <= 16) or not (0.0 < x0 <= 0.5):
-        raise ValueError("need 1 <= W <= 16 and 0 < x0 <= 0.5")
+def _minimise(W: int, x0: float, degree: int, nx: int, n_nu: int, max_iter: int, vec0=None):
+    """Minimise the quadrature form of E^2 over the even-C coefficients, h eliminated.
+
+    Each iteration takes the Gauss-Newton step (least squares on the Jacobian of
+    the residual, not the normal equations), halved until E^2 falls.  Where no
+    halving helps, it takes a Levenberg-Marquardt step instead: the same least
+    squares with the damping term mu |diag(|J_p|) step|^2, mu raised until E^2
+    falls.  Stops when neither lowers E^2 or the relative gain is below 1e-10.
+    Returns (coefficient vector, parameter map, h at the x nodes, x nodes).
+    """
     xq, wx = gauss_legendre(nx, -x0, x0)
     nq, wn = gauss_legendre(n_nu, -0.5, 0.5)
     s = tap_offsets(W)
     cols, B = _parameter_map(W, degree, nq)
-    npar = len(cols)
     E = np.exp(2j * np.pi * (s[None, None, :] - nq[None, :, None]) * xq[:, None, None])
     A = np.einsum("pnw,xnw->pxn", B, E)                     # d a(x,nu) / d beta_p
     sq = np.sqrt(wx[:, None] * wn[None, :])
@@ -230,31 +238,83 @@ def least_misfit(W: int, x0: float, degree: int = 20, nx: int = 64,
         obj = float((wx[:, None] * wn[None, :] * np.abs(rho) ** 2).sum() / (2.0 * x0))
         return a, R, Q, h, rho, obj
 
-    # start: the best C for h = 1 (one exact partial minimisation)
-    y = np.concatenate([sq.ravel(), np.zeros(sq.size)])
-    vec = np.linalg.lstsq(realify(A), y, rcond=None)[0]
+    if vec0 is None:
+        # start: the best C for h = 1 (one exact partial minimisation)
+        y = np.concatenate([sq.ravel(), np.zeros(sq.size)])
+        vec = np.linalg.lstsq(realify(A), y, rcond=None)[0]
+    else:
+        vec = np.asarray(vec0, dtype=np.float64)
     a, R, Q, h, rho, obj = state(vec)
     for _ in range(max_iter):
         dR = (wn[None, None, :] * A.real).sum(2)                                  # (p, x)
         dQ = 2.0 * (wn[None, None, :] * (np.conj(a)[None] * A).real).sum(2)
         dh = dR / Q[None] - (R / Q ** 2)[None] * dQ
-        J = -(dh[:, :, None] * a[None] + h[None, :, None] * A)
+        J = realify(-(dh[:, :, None] * a[None] + h[None, :, None] * A))
         rr = np.concatenate([(sq * rho).real.ravel(), (sq * rho).imag.ravel()])
-        step = np.linalg.lstsq(realify(J), -rr, rcond=1e-14)[0]
-        lam, improved = 1.0, False
-        while lam > 1e-8:
-            cand = state(vec + lam * step)
-            if cand[-1] < obj:
-                improved = True
+        # one SVD of the column-scaled Jacobian J diag(1/scale) = U S V^T serves both
+        # steps: Gauss-Newton (pseudo-inverse, singular values below 1e-14 S_max
+        # dropped) and Levenberg-Marquardt (S / (S^2 + mu))
+        scale = np.linalg.norm(J, axis=0)
+        scale[scale == 0.0] = 1.0
+        U, S, Vt = np.linalg.svd(J / scale[None, :], full_matrices=False)
+        g = U.T @ rr
+
+        def step_for(filt):
+            return -(Vt.T @ (filt * g)) / scale
+
+        keep = S > 1e-14 * S[0]
+        step = step_for(np.where(keep, 1.0 / np.where(keep, S, 1.0), 0.0))
+        lam, cand = 1.0, None
+        while lam > 1e-4:
+            trial = state(vec + lam * step)
+            if trial[-1] < obj:
+                cand, step = trial, lam * step
                 break
             lam *= 0.5
-        if not improved:
+        mu = 1e-8
+        while cand is None and mu < 1e12:
+            step = step_for(S / (S * S + mu))
+            trial = state(vec + step)
+            if trial[-1] < obj:
+                cand = trial
+            mu *= 4.0
+        if cand is None:
             break
         rel = (obj - cand[-1]) / obj
-        vec = vec + lam * step
+        vec = vec + step
         a, R, Q, h, rho, obj = cand
-        if rel < 1e-9:
+        if rel < 1e-10:
             break
+    return vec, cols, h, xq
+
+
+# Above this cropping parameter the fit is followed from x0 = 1/4 upward.
+_CONTINUE_ABOVE = 0.3
+_CONTINUE_STEP = 0.05
+
+
+@lru_cache(maxsize=64)
+def least_misfit(W: int, x0: float, degree: int = 20, nx: int = 64,
+                 n_nu: int = 64, max_iter: int = 60) -> LeastMisfit:
+    """Minimise E over even C (support W) and real h for cropping parameter x0.
+
+    For x0 above 0.3 the minimiser is followed from x0 = 1/4 in steps of 0.05,
+    each fit starting from the previous one's coefficients: started cold at
+    large x0 (from the best C for h = 1), the iteration can settle in a poorer
+    local minimum, which it did at W = 8, 12 and 14 with x0 = 0.4 - 0.45 (E
+    then fails to fall with W).
+    """
+    if not (1 <= W <= 16) or not (0.0 < x0 <= 0.5):
+        raise ValueError("need 1 <= W <= 16 and 0 < x0 <= 0.5")
+    path = [float(x0)]
+    if x0 > _CONTINUE_ABOVE:
+        path = [0.25]
+        while path[-1] + _CONTINUE_STEP < x0 - 1e-12:
+            path.append(path[-1] + _CONTINUE_STEP)
+        path.append(float(x0))
+    vec = None
+    for xs in path:
+        vec, cols, h, xq = _minimise(W, xs, degree, nx, n_nu, max_iter, vec)
     beta = _expand(cols, vec, W, degree)
     beta = beta * h[np.argmin(np.abs(xq))]                  # gauge: h(0) ~ 1 (h scales as 1/beta)
     lm = LeastMisfit(W=W, x0=float(x0), beta=beta, E=float("nan"))

@@ -23,8 +23,8 @@ STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_ARG", 2: "WS_ERR_UV_RANGE", 3: "WS_ERR_W_
                 4: "WS_ERR_CUDA", 5: "WS_ERR_OOM", 6: "WS_ERR_TIMEOUT"}
 
 # every entry point declared in include/ws.h
-EXPORTS = ("ws_plan", "ws_plan_original", "ws_degrid", "ws_grid", "ws_degrid_noalloc", "ws_plan_dropped", "ws_plan_info",
-           "ws_plan_stats", "ws_destroy", "ws_batch_create", "ws_batch_grid", "ws_batch_degrid",
+EXPORTS = ("ws_plan", "ws_plan_original", "ws_degrid", "ws_grid", "ws_plan_bind_uvw", "ws_degrid_noalloc",
+           "ws_plan_dropped", "ws_plan_info", "ws_plan_stats", "ws_destroy", "ws_batch_create", "ws_batch_grid", "ws_batch_degrid",
            "ws_batch_info", "ws_batch_branches", "ws_batch_destroy", "ws_last_error")
 
 
@@ -78,6 +78,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
     lib.ws_plan_original.argtypes = [ctypes.POINTER(vp), i32, dbl, i32, dbl, dbl, dbl, i32, u32]
     lib.ws_degrid.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_grid.argtypes = [vp, vp, vp, i64, vp, vp]
+    lib.ws_plan_bind_uvw.argtypes = [vp, vp, i64, vp]
     lib.ws_degrid_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_plan_dropped.argtypes = [vp, ctypes.POINTER(i64)]
     lib.ws_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
@@ -132,6 +133,11 @@ def ws_grid(plan: int, uvw_ptr: int, vis_ptr: int, M: int, dirty_ptr: int, strea
     if st not in (WS_OK, WS_ERR_UV_RANGE, WS_ERR_W_RANGE):
         _check(st)
     return st
+
+
+def ws_plan_bind_uvw(plan: int, uvw_ptr: int, M: int, stream: int = 0) -> None:
+    """Pre-process and bin a uvw set once for later calls with the same pointer and M (0 unbinds)."""
+    _check(load().ws_plan_bind_uvw(plan, uvw_ptr, M, stream))
 
 
 def ws_degrid_noalloc(plan: int, image_ptr: int, uvw_ptr: int, M: int, vis_ptr: int, stream: int = 0) -> int:

@@ -41,7 +41,11 @@ class DegridFunction(torch.autograd.Function):
 
 
 def degrid(plan: Plan, image: torch.Tensor, uvw: torch.Tensor) -> torch.Tensor:
-    """Differentiable degridding: visibilities of ``image`` at ``uvw`` (see DegridFunction)."""
+    """Differentiable degridding: visibilities of ``image`` at ``uvw`` (see DegridFunction).
+
+    An optimisation loop calls this with the same uvw every step; binding it to
+    the plan once (``plan.bind(uvw)``) lets the forward and backward calls skip
+    the tap rule and the tile sort."""
     return DegridFunction.apply(image, uvw, plan)
 
 

@@ -89,6 +89,14 @@ void release(ws_plan_s *p) {
     cudaFree(p->d_img);
     cudaFree(p->d_drop);
     cudaFree(p->d_occ_counts);
+    cudaFree(p->d_brec);
+    cudaFree(p->d_blist_g);
+    cudaFree(p->d_blist_d);
+    cudaFree(p->d_boff_g);
+    cudaFree(p->d_boff_d);
+    cudaFree(p->d_btile_occ);
+    cudaFree(p->d_bcol_occ);
+    cudaFree(p->d_bdrop);
     if (p->h_drop) cudaFreeHost(p->h_drop);
     if (p->h_occ_counts) cudaFreeHost(p->h_occ_counts);
     delete p;
@@ -608,20 +616,66 @@ fail:
     return st;
 }
 
+namespace {
+
+// For the scope of one call on the bound visibility set: the plan's tile
+// lists, offsets and occupancy maps (and, for degridding, its records) are
+// the bound set's.  A plan serves one call at a time, so the swap is private
+// to the call; the destructor puts the per-call buffers back.
+struct BoundView {
+    ws_plan_s *p;
+    bool active;
+    VisRec *rec;
+    uint32_t *list, *offsets;
+    uint8_t *tile_occ, *col_occ;
+    BoundView(ws_plan_s *p_, bool active_, bool grid)
+        : p(p_), active(active_), rec(p_->d_rec), list(p_->d_list), offsets(p_->d_offsets),
+          tile_occ(p_->d_tile_occ), col_occ(p_->d_col_occ) {
+        if (!active) return;
+        if (!grid) p->d_rec = p->d_brec;
+        p->d_list = grid ? p->d_blist_g : p->d_blist_d;
+        p->d_offsets = grid ? p->d_boff_g : p->d_boff_d;
+        p->d_tile_occ = p->d_btile_occ;
+        p->d_col_occ = p->d_bcol_occ;
+    }
+    ~BoundView() {
+        p->d_rec = rec;
+        p->d_list = list;
+        p->d_offsets = offsets;
+        p->d_tile_occ = tile_occ;
+        p->d_col_occ = col_occ;
+    }
+};
+
+bool is_bound(const ws_plan_s *p, const double *uvw, int64_t M) {
+    return p->b_uvw != nullptr && uvw == p->b_uvw && M == p->b_M;
+}
+
+}  // namespace
+
 ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, float2 *dirty,
                        cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, kCounters * sizeof(unsigned long long), s);
+    const bool bound = is_bound(p, uvw, M);
+    cudaError_t e = bound ? cudaMemcpyAsync(p->d_drop, p->d_bdrop, kCounters * sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToDevice, s)
+                          : cudaMemsetAsync(p->d_drop, 0, kCounters * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "ws_grid: clearing counters");
     p->stats.calls += 1;
-    {
+    if (bound) {
+        // the bound set's records, with this call's values and the gridding pre-phase
         StageTimer t(p, s, WS_STAGE_PREP, M > 0 ? 1 : 0);
-        if ((e = launch_prep(p, uvw, vis, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: prep kernel");
-    }
-    {
+        if ((e = launch_bound_grid_records(p, uvw, vis, M, s)) != cudaSuccess)
+            return cuda_fail(e, "ws_grid: bound records kernel");
+    } else {
+        {
+            StageTimer t(p, s, WS_STAGE_PREP, M > 0 ? 1 : 0);
+            if ((e = launch_prep(p, uvw, vis, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: prep kernel");
+        }
         StageTimer t(p, s, WS_STAGE_BIN, (M > 0 ? 6 : 3) + ((p->flags & WS_FLAG_TIMING) ? 1 : 0));
         if ((e = launch_bin(p, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: binning kernels");
         if ((e = launch_mark_grid(p, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy kernel");
     }
+    BoundView view(p, bound, true);
     if ((e = copy_occ_counts(p, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy statistics");
     // test knob: the poll limit of inv_rows' first wait for each plane's row copy
     p->wait_polls = kWaitPolls;
@@ -654,22 +708,26 @@ ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64
 
 ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, int64_t M, float2 *vis,
                          cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_drop, 0, kCounters * sizeof(unsigned long long), s);
+    const bool bound = is_bound(p, uvw, M);
+    cudaError_t e = bound ? cudaMemcpyAsync(p->d_drop, p->d_bdrop, kCounters * sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToDevice, s)
+                          : cudaMemsetAsync(p->d_drop, 0, kCounters * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "ws_degrid: clearing counters");
     if (M == 0) return WS_OK;
     if ((e = cudaMemsetAsync(vis, 0, (size_t)M * sizeof(float2), s)) != cudaSuccess)
         return cuda_fail(e, "ws_degrid: clearing the output");
     p->stats.calls += 1;
-    {
-        StageTimer t(p, s, WS_STAGE_PREP, 1);
-        if ((e = launch_prep(p, uvw, nullptr, M, false, s)) != cudaSuccess)
-            return cuda_fail(e, "ws_degrid: prep kernel");
-    }
-    {
+    if (!bound) {
+        {
+            StageTimer t(p, s, WS_STAGE_PREP, 1);
+            if ((e = launch_prep(p, uvw, nullptr, M, false, s)) != cudaSuccess)
+                return cuda_fail(e, "ws_degrid: prep kernel");
+        }
         StageTimer t(p, s, WS_STAGE_BIN, 7 + ((p->flags & WS_FLAG_TIMING) ? 1 : 0));
         if ((e = launch_bin(p, M, false, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: binning kernels");
         if ((e = launch_mark(p, M, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy kernel");
     }
+    BoundView view(p, bound, false);
     if ((e = copy_occ_counts(p, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy statistics");
     {
         StageTimer t(p, s, WS_STAGE_CORRECT, 1);
@@ -755,6 +813,94 @@ ws_status ws_plan_dropped(ws_plan_t plan, int64_t *dropped) {
     if (e != cudaSuccess) return cuda_fail(e, "ws_plan_dropped: synchronize");
     plan->last_dropped = (int64_t)(plan->h_drop[0] + plan->h_drop[1]);
     *dropped = plan->last_dropped;
+    return WS_OK;
+}
+
+ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stream_t stream) {
+    if (!plan || M < 0 || M > kMaxVis) {
+        set_error("ws_plan_bind_uvw: invalid argument");
+        return WS_ERR_ARG;
+    }
+    ws_plan_s *p = plan;
+    p->b_uvw = nullptr;                      // invalid until the new set is complete
+    p->b_M = -1;
+    if (!uvw) return WS_OK;
+    DeviceScope scope(p->dev);
+    if (!scope.ok) {
+        set_error("ws_plan_bind_uvw: cannot select the plan's device");
+        return WS_ERR_CUDA;
+    }
+    const int64_t Mc = std::max<int64_t>(M, 1);
+    const int64_t per = 4 * ((p->L.W - 1 + TT - 1) / TT + 1);     // footprint tiles per visibility, at most
+    cudaError_t e = cudaSuccess;
+    auto grow = [&](auto **ptr, int64_t *cap, int64_t need, const char *what) -> bool {
+        if (need <= *cap) return true;
+        cudaFree(*ptr);
+        p->bytes -= *cap * (int64_t)sizeof(**ptr);
+        *cap = 0;
+        if ((e = dev_alloc(ptr, (size_t)need, &p->bytes)) != cudaSuccess) {
+            cuda_fail(e, what);
+            return false;
+        }
+        *cap = need;
+        return true;
+    };
+    if (!grow(&p->d_brec, &p->brec_cap, Mc, "ws_plan_bind_uvw: allocating records") ||
+        !grow(&p->d_blist_g, &p->blist_g_cap, Mc * per, "ws_plan_bind_uvw: allocating gridding lists") ||
+        !grow(&p->d_blist_d, &p->blist_d_cap, Mc, "ws_plan_bind_uvw: allocating degridding lists"))
+        return e == cudaErrorMemoryAllocation ? WS_ERR_OOM : WS_ERR_CUDA;
+    if (!p->d_boff_g) {
+        const char *what = nullptr;
+        if ((e = dev_alloc(&p->d_boff_g, (size_t)p->ntiles + 1, &p->bytes)) != cudaSuccess) what = "offsets";
+        else if ((e = dev_alloc(&p->d_boff_d, (size_t)p->ntiles + 1, &p->bytes)) != cudaSuccess) what = "offsets";
+        else if ((e = dev_alloc(&p->d_btile_occ, (size_t)p->ntiles, &p->bytes)) != cudaSuccess) what = "occupancy";
+        else if ((e = dev_alloc(&p->d_bcol_occ, (size_t)p->L.ntt * p->L.ntu, &p->bytes)) != cudaSuccess) what = "occupancy";
+        else if ((e = dev_alloc(&p->d_bdrop, (size_t)kCounters, &p->bytes)) != cudaSuccess) what = "counters";
+        if (what) {
+            ws_status st = cuda_fail(e, "ws_plan_bind_uvw: allocating the bound set's tables");
+            cudaFree(p->d_boff_g);
+            cudaFree(p->d_boff_d);
+            cudaFree(p->d_btile_occ);
+            cudaFree(p->d_bcol_occ);
+            cudaFree(p->d_bdrop);
+            p->d_boff_g = p->d_boff_d = nullptr;
+            p->d_btile_occ = p->d_bcol_occ = nullptr;
+            p->d_bdrop = nullptr;
+            return st;
+        }
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((e = cudaMemsetAsync(p->d_drop, 0, kCounters * sizeof(unsigned long long), s)) != cudaSuccess)
+        return cuda_fail(e, "ws_plan_bind_uvw: clearing counters");
+    {
+        // records in the degridding form, both directions' lists and the occupancy,
+        // written straight into the bound set's buffers
+        VisRec *rec = p->d_rec;
+        uint32_t *list = p->d_list, *offsets = p->d_offsets;
+        uint8_t *tile_occ = p->d_tile_occ, *col_occ = p->d_col_occ;
+        p->d_rec = p->d_brec;
+        p->d_list = p->d_blist_g;
+        p->d_offsets = p->d_boff_g;
+        p->d_tile_occ = p->d_btile_occ;
+        p->d_col_occ = p->d_bcol_occ;
+        e = launch_prep(p, uvw, nullptr, M, false, s);
+        if (e == cudaSuccess) e = launch_bin(p, M, true, s);
+        if (e == cudaSuccess) e = launch_mark_grid(p, s);
+        p->d_list = p->d_blist_d;
+        p->d_offsets = p->d_boff_d;
+        if (e == cudaSuccess) e = launch_bin(p, M, false, s);
+        p->d_rec = rec;
+        p->d_list = list;
+        p->d_offsets = offsets;
+        p->d_tile_occ = tile_occ;
+        p->d_col_occ = col_occ;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->d_bdrop, p->d_drop, kCounters * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "ws_plan_bind_uvw: pre-processing and binning");
+    p->b_uvw = uvw;
+    p->b_M = M;
     return WS_OK;
 }
 

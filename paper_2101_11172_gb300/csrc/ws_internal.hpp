@@ -90,6 +90,21 @@ struct ws_plan_s {
     unsigned long long *d_drop = nullptr;   // kCounters: [0] non-finite uv, [1] w out of range, [2] timed-out waits
     unsigned long long *h_drop = nullptr;   // pinned mirror
     int wait_polls = ws::kWaitPolls;        // limit of inv_rows' first wait per plane (WS_WAIT_POLLS)
+    // visibility set bound by ws_plan_bind_uvw: records (degridding form) and
+    // both directions' tile lists, made once for that uvw
+    const double *b_uvw = nullptr;
+    int64_t b_M = -1;
+    ws::VisRec *d_brec = nullptr;
+    int64_t brec_cap = 0;
+    uint32_t *d_blist_g = nullptr;          // gridding: (visibility, footprint tile) pairs by tile
+    int64_t blist_g_cap = 0;
+    uint32_t *d_blist_d = nullptr;          // degridding: visibilities by first-tap tile
+    int64_t blist_d_cap = 0;
+    uint32_t *d_boff_g = nullptr;           // ntiles + 1
+    uint32_t *d_boff_d = nullptr;           // ntiles + 1
+    uint8_t *d_btile_occ = nullptr;         // ntiles
+    uint8_t *d_bcol_occ = nullptr;          // ntt x ntu
+    unsigned long long *d_bdrop = nullptr;  // kCounters: the bound set's drop counts
     // occupancy statistics (WS_FLAG_TIMING): per t-tile, occupied tiles and
     // (t-tile, u-strip) strips, then the number of tile-list entries
     uint32_t *d_occ_counts = nullptr;       // 2 ntt
@@ -127,6 +142,8 @@ ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, i
 // Launchers (wstack.cu).
 cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,
                         bool grid, cudaStream_t s);
+cudaError_t launch_bound_grid_records(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,
+                                      cudaStream_t s);
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
 cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s);
 cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s);

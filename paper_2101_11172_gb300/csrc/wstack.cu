@@ -95,6 +95,22 @@ __global__ void prep_kernel(Launch L, const double *__restrict__ uvw, const floa
     rec[k] = r;
 }
 
+// Gridding records of a bound visibility set: the set's records hold the
+// degridding factor exp(-2 pi i w (n0 - 1)); gridding needs V exp(+2 pi i w
+// (n0 - 1)), with V conjugated where a real-sky plan folded w < 0.
+__global__ void bound_grid_records_kernel(Launch L, const double *__restrict__ uvw, const float2 *__restrict__ vis,
+                                          int64_t M, const VisRec *__restrict__ brec, VisRec *__restrict__ rec) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M) return;
+    VisRec r = brec[k];
+    float2 V = vis[k];
+    if (L.fold && uvw[3 * k + 2] < 0.0) V.y = -V.y;
+    const float c = r.vre, s = -r.vim;      // exp(+2 pi i w (n0 - 1)) = (c, s)
+    r.vre = V.x * c - V.y * s;
+    r.vim = V.x * s + V.y * c;
+    rec[k] = r;
+}
+
 // ---------------------------------------------------------------------------
 // Binning: counting sort of (visibility, tile) pairs by tile id
 // ---------------------------------------------------------------------------
@@ -254,10 +270,52 @@ __global__ void scan_add_kernel(uint32_t *__restrict__ out, const uint32_t *__re
 // Gridding: Algorithm 5 steps 2 and 3a (Eq. gridded_vis).  One CTA owns one
 // TT x TV x TU tile of the stack chunk, accumulates every (visibility, tile)
 // pair of its list in shared memory and writes the tile exactly once.
+//
+// The tile's entries are split evenly over the CTA's warps; a warp takes its
+// share in chunks of up to kChunk entries, in three steps:
+//   1. lane j prepares entry j of the chunk: its record, the part of its
+//      W x W x W footprint that lies in the tile (first tap and tap count
+//      along u, v and w) and the tile offset of that part's first cell;
+//   2. the warp evaluates the chunk's 3W weight polynomials C(r - u'),
+//      C(s - v'), C(t - w'), one (entry, slot) pair per lane and round;
+//   3. entry after entry, the lanes take the (row, plane) pairs of the part,
+//      form C_y C_z V once each, and add C_x C_y C_z V along the part's run of
+//      u taps with shared-memory reductions at immediate offsets.
+// So the tap rule, the index arithmetic and the polynomials cost once per
+// entry, and each tap costs one weight product and one reduction per
+// component.
 // ---------------------------------------------------------------------------
 constexpr int kGridThreads = 256;
-constexpr int kRowPad = TU + 1;                 // shared row stride: rows b and b + 2 fall in different banks
-constexpr int kTileSlots = TT * TV * kRowPad;
+constexpr int kGridWarps = kGridThreads / 32;
+constexpr int kRowPad = TU + 1;                    // shared row stride (floats)
+// Shared plane stride: 552 = 8 (mod 32), so (17 b + 552 c) mod 32 differs for
+// every b < 7 and c < 4: the (row, plane) pairs of one pass hit distinct banks.
+constexpr int kPlaneStride = TV * kRowPad + 8;
+constexpr int kTileFloats = TT * kPlaneStride;
+constexpr int kCoefStride = 20;                    // kMaxDeg + 1 coefficients per slot, padded for float4 loads
+static_assert(kMaxDeg + 1 <= kCoefStride && kCoefStride % 4 == 0 && kMaxDeg == 16,
+              "the Horner steps below read coefficients 0..16 as five float4");
+static_assert(kTileFloats % 4 == 0, "the tile is cleared in float4 stores");
+static_assert(kMaxW <= 15, "tap counts and first taps are packed in 4 bits");
+constexpr int kGeneral = -1;                       // item shape: the part wraps an axis of a small grid
+constexpr int kChunk = 16;                         // entries a warp stages at a time
+
+// Dynamic shared memory of grid3d<W>: the tile (re, im), the weight table,
+// and per warp the staged chunk (weights, items, values, offsets nu).
+template <int W>
+struct GridSmem {
+    static constexpr int S = 3 * W;                // weight slots per entry: u taps, v taps, w taps
+    static constexpr int SP = S | 1;               // entry stride of the staged weights
+    static constexpr size_t re = 0;
+    static constexpr size_t im = re + (size_t)kTileFloats * 4;
+    static constexpr size_t coef = im + (size_t)kTileFloats * 4;
+    static constexpr size_t wt = coef + (size_t)S * kCoefStride * 4;
+    static constexpr size_t item = wt + (size_t)kGridWarps * kChunk * SP * 4;
+    static constexpr size_t val = item + (size_t)kGridWarps * kChunk * 16;
+    static constexpr size_t nu = val + (size_t)kGridWarps * kChunk * 8;
+    static constexpr size_t bytes = nu + (size_t)kGridWarps * kChunk * 16;
+    static_assert(coef % 16 == 0 && wt % 16 == 0 && item % 16 == 0 && nu % 16 == 0, "float4 / int4 alignment");
+};
 
 // Taps [a0, a1) of a footprint that land in a tile, at tile-local index a - off.
 struct Span {
@@ -267,7 +325,8 @@ struct Span {
 // The footprint covers positions first .. first + W - 1 and the tile org ..
 // org + T - 1 of a periodic axis of length n >= T: the tile starts d = org -
 // first (mod n) past the footprint's start, and if it runs past n it also
-// covers the footprint's first d + T - n positions.  Returns 0, 1 or 2 spans.
+// covers the footprint's first d + T - n positions.  Returns 0, 1 or 2 spans
+// (two only when n < W + T, a grid of 32 rows).
 __device__ __forceinline__ int tile_spans(int org, int first, int n, int W, int T, Span &s0, Span &s1) {
     int d = org - first;
     if (d < 0) d += n;
@@ -278,101 +337,165 @@ __device__ __forceinline__ int tile_spans(int org, int first, int n, int W, int 
     return (int)has_inside + (int)has_wrapped;
 }
 
-// Shared-memory FP32 add with no returned value.
-__device__ __forceinline__ void red_add_shared(float *addr, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(addr)), "f"(v) : "memory");
+// Shared-memory FP32 add with no returned value, at a byte offset fixed at compile time.
+template <int OFF>
+__device__ __forceinline__ void red_shared_at(unsigned addr, float v) {
+    asm volatile("red.shared.add.f32 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_shared(unsigned addr, float v) {
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a tile row (re and im at byte addresses).
+template <int W, int A = 0>
+__device__ __forceinline__ void add_row(unsigned re, unsigned im, const float *wx, int na, float pr, float pi) {
+    if constexpr (A < W) {
+        if (A < na) {
+            const float w = wx[A];
+            red_shared_at<4 * A>(re, pr * w);
+            red_shared_at<4 * A>(im, pi * w);
+            add_row<W, A + 1>(re, im, wx, na, pr, pi);
+        }
+    }
 }
 
 template <int W>
-__global__ void __launch_bounds__(kGridThreads, 6)
+__global__ void __launch_bounds__(kGridThreads, 4)
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
               uint32_t tile_base, int chunk_tt0, float2 *__restrict__ stack) {
-    __shared__ __align__(16) float sre[kTileSlots];
-    __shared__ __align__(16) float sim[kTileSlots];
-    __shared__ float swt[kGridThreads / 32][3 * W];
-    __shared__ float scoef[kMaxDeg + 1][3 * W];       // [m][slot]: weight slot l's polynomial, zero-padded
+    using Sm = GridSmem<W>;
+    constexpr int S = Sm::S, SP = Sm::SP;
+    extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t tile = tile_base + blockIdx.x;
-    if (offsets[tile] == offsets[tile + 1]) return;   // empty tile: the transforms treat it as zero
+    const uint32_t beg = offsets[tile], end = offsets[tile + 1];
+    if (beg == end) return;                           // empty tile: the transforms treat it as zero
+    float *sre = reinterpret_cast<float *>(smem + Sm::re);
+    float *sim = reinterpret_cast<float *>(smem + Sm::im);
+    float *scoef = reinterpret_cast<float *>(smem + Sm::coef);
     const int tu = tile % L.ntu;
     const int tv = (tile / L.ntu) % L.ntv;
     const int tt = tile / (L.ntu * L.ntv);
-    static_assert(kTileSlots % 4 == 0, "the tile is cleared in float4 stores");
-    for (int i = threadIdx.x; i < kTileSlots / 4; i += kGridThreads) {
+    for (int i = threadIdx.x; i < kTileFloats / 4; i += kGridThreads) {
         reinterpret_cast<float4 *>(sre)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         reinterpret_cast<float4 *>(sim)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const int Np = L.Np;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // weight slot l < 3W is (axis l / W, tap l % W); lane l evaluates slots l and
-    // l + 32.  coef holds the (u, v) table and then the w table, W x (deg + 1) each.
-    for (int i = threadIdx.x; i < (kMaxDeg + 1) * 3 * W; i += kGridThreads) {
-        const int m = i / (3 * W), l = i % (3 * W), axis = l / W, tap = l - axis * W;
+    // slot l < 3W is (axis l / W, tap l % W); coef holds the (u, v) table and
+    // then the w table, W x (deg + 1) each; coefficients past deg are zero
+    for (int i = threadIdx.x; i < S * kCoefStride; i += kGridThreads) {
+        const int l = i / kCoefStride, m = i - l * kCoefStride, axis = l / W, tap = l - axis * W;
         const int row = (axis == 2 ? W : 0) + tap;
-        scoef[m][l] = m <= deg ? coef[row * (deg + 1) + m] : 0.f;
+        scoef[i] = m <= deg ? coef[row * (deg + 1) + m] : 0.f;
     }
     __syncthreads();
-    const uint32_t beg = offsets[tile], end = offsets[tile + 1];
+    const int Np = L.Np;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int u_org = tu * TU, v_org = tv * TV, t_org = tt * TT;
-    float *wt = swt[warp];
-    for (uint32_t e = beg + warp; e < end; e += kGridThreads / 32) {
-        const VisRec r = rec[list[e]];
-        // slot lane, and slot lane + 32 where 3W > 32 (W >= 11)
-#pragma unroll
-        for (int h = 0; h < (3 * W + 31) / 32; ++h) {
-            const int l = lane + 32 * h;
-            if (l < 3 * W) {
-                const int axis = l / W;
-                const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
-                float acc = scoef[kMaxDeg][l];
-#pragma unroll
-                for (int m = kMaxDeg - 1; m >= 0; --m) acc = fmaf(acc, nu, scoef[m][l]);
-                wt[l] = acc;
+    float *wts = reinterpret_cast<float *>(smem + Sm::wt) + warp * kChunk * SP;
+    int4 *items = reinterpret_cast<int4 *>(smem + Sm::item) + warp * kChunk;
+    float2 *vals = reinterpret_cast<float2 *>(smem + Sm::val) + warp * kChunk;
+    float4 *nus = reinterpret_cast<float4 *>(smem + Sm::nu) + warp * kChunk;
+    const unsigned re_base = (unsigned)__cvta_generic_to_shared(sre);
+    const unsigned im_base = (unsigned)__cvta_generic_to_shared(sim);
+    // this warp's share of the tile's entries
+    const uint32_t E = end - beg, per = (E + kGridWarps - 1) / kGridWarps;
+    const uint32_t wbeg = beg + min(E, warp * per), wend = beg + min(E, (warp + 1) * per);
+    for (uint32_t cbeg = wbeg; cbeg < wend; cbeg += kChunk) {
+        const int n = (int)min((uint32_t)kChunk, wend - cbeg);
+        // 1. lane j: entry j's part of the footprint inside the tile
+        if (lane < n) {
+            const uint32_t k = list[cbeg + lane];
+            const VisRec r = rec[k];
+            Span su[2], sv[2];
+            const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
+            const int nsv = tile_spans(v_org, r.s0, Np, W, TV, sv[0], sv[1]);
+            const int dt = t_org - r.t0;
+            const int c0 = max(0, dt), c1 = min(W, dt + TT);
+            int4 it;
+            if (nsu == 1 && nsv == 1) {
+                const int na = su[0].a1 - su[0].a0, nb = sv[0].a1 - sv[0].a0, nc = c1 - c0;
+                it.x = (c0 - dt) * kPlaneStride + (sv[0].a0 - sv[0].off) * kRowPad + (su[0].a0 - su[0].off);
+                it.y = na | nb << 4 | max(nc, 0) << 8 | su[0].a0 << 12 | sv[0].a0 << 16 | c0 << 20;
+                it.z = __float_as_int(1.0f / (float)nb);
+            } else {
+                it.x = 0;
+                it.y = kGeneral;
+                it.z = 0;
             }
+            it.w = (int)k;
+            items[lane] = it;
+            vals[lane] = make_float2(r.vre, r.vim);
+            nus[lane] = make_float4(r.nux, r.nuy, r.nuz, 0.f);
         }
         __syncwarp();
-        // the part of the W x W x W footprint inside this tile: taps along u and v
-        // (one span each, two where the tile wraps past the footprint) and planes
-        // c in [c0, c1) at tile plane c - dt
-        Span su[2], sv[2];
-        const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
-        const int nsv = tile_spans(v_org, r.s0, Np, W, TV, sv[0], sv[1]);
-        const int dt = t_org - r.t0;
-        const int c0 = max(0, dt), c1 = min(W, dt + TT);
+        // 2. the chunk's weights: pair q = (entry j, slot l), Horner from nu^16 down
+        for (int q = lane; q < n * S; q += 32) {
+            const int j = q / S, l = q - j * S, axis = l / W;
+            const float4 nv = nus[j];
+            const float nu = axis == 0 ? nv.x : (axis == 1 ? nv.y : nv.z);
+            const float4 *c = reinterpret_cast<const float4 *>(scoef + l * kCoefStride);
+            float acc = c[4].x;
 #pragma unroll
-        for (int iu = 0; iu < 2; ++iu) {
-            if (iu >= nsu) break;
-#pragma unroll
-            for (int iv = 0; iv < 2; ++iv) {
-                if (iv >= nsv) break;
-                const int na = su[iu].a1 - su[iu].a0, nab = na * (sv[iv].a1 - sv[iv].a0);
-                const float inv_na = 1.0f / (float)na;
-                for (int q = lane; q < nab; q += 32) {
-                    // q = bb na + aa, q < 144: (q + 1/2) / na is at least 1/24 from an integer
-                    const int bb = __float2int_rz(((float)q + 0.5f) * inv_na), aa = q - bb * na;
-                    const int a = su[iu].a0 + aa, b = sv[iv].a0 + bb;
-                    const float wxy = wt[a] * wt[W + b];
-                    const float vr = r.vre * wxy, vi = r.vim * wxy;
-                    int idx = ((c0 - dt) * TV + (b - sv[iv].off)) * kRowPad + (a - su[iu].off);
-                    for (int c = c0; c < c1; ++c, idx += TV * kRowPad) {
-                        const float wz = wt[2 * W + c];
-                        red_add_shared(&sre[idx], vr * wz);
-                        red_add_shared(&sim[idx], vi * wz);
-                    }
+            for (int b = 3; b >= 0; --b) {
+                const float4 c4 = c[b];
+                acc = fmaf(acc, nu, c4.w);
+                acc = fmaf(acc, nu, c4.z);
+                acc = fmaf(acc, nu, c4.y);
+                acc = fmaf(acc, nu, c4.x);
+            }
+            wts[j * SP + l] = acc;
+        }
+        __syncwarp();
+        // 3. add the chunk's entries one after the other
+        for (int j = 0; j < n; ++j) {
+            const int4 it = items[j];
+            const float2 V = vals[j];
+            const float *wt = wts + j * SP;
+            if (it.y != kGeneral) {
+                const int na = it.y & 15, nb = (it.y >> 4) & 15, nc = (it.y >> 8) & 15;
+                const int a0 = (it.y >> 12) & 15, b0 = (it.y >> 16) & 15, cw0 = (it.y >> 20) & 15;
+                const float inv_nb = __int_as_float(it.z);
+                const int nbc = nb * nc;
+                for (int q = lane; q < nbc; q += 32) {
+                    // q = cc nb + bb, q < 144: (q + 1/2) / nb is at least 1/24 from an integer
+                    const int cc = __float2int_rz(((float)q + 0.5f) * inv_nb), bb = q - cc * nb;
+                    const float wyz = wt[W + b0 + bb] * wt[2 * W + cw0 + cc];
+                    const unsigned off = (unsigned)(it.x + cc * kPlaneStride + bb * kRowPad) * 4u;
+                    add_row<W>(re_base + off, im_base + off, wt + a0, na, V.x * wyz, V.y * wyz);
                 }
+            } else {
+                // the part wraps around an axis (N' < W + TV): every span pair, taps one by one
+                const VisRec r = rec[it.w];
+                Span su[2], sv[2];
+                const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
+                const int nsv = tile_spans(v_org, r.s0, Np, W, TV, sv[0], sv[1]);
+                const int dt = t_org - r.t0;
+                const int c0 = max(0, dt), c1 = min(W, dt + TT);
+                for (int iu = 0; iu < nsu; ++iu)
+                    for (int iv = 0; iv < nsv; ++iv) {
+                        const int na = su[iu].a1 - su[iu].a0, nb = sv[iv].a1 - sv[iv].a0, nc = c1 - c0;
+                        for (int q = lane; q < na * nb * nc; q += 32) {
+                            const int a = su[iu].a0 + q % na, b = sv[iv].a0 + (q / na) % nb, c = c0 + q / (na * nb);
+                            const float w = wt[a] * wt[W + b] * wt[2 * W + c];
+                            const unsigned off =
+                                (unsigned)((c - dt) * kPlaneStride + (b - sv[iv].off) * kRowPad + (a - su[iu].off)) * 4u;
+                            red_shared(re_base + off, V.x * w);
+                            red_shared(im_base + off, V.y * w);
+                        }
+                    }
             }
         }
-        __syncwarp();
+        __syncwarp();                                  // the chunk's staging is read before the next overwrites it
     }
     __syncthreads();
     const size_t plane = (size_t)Np * Np;
     const int p0 = t_org - chunk_tt0 * TT;
     // pairs of cells, ordered (plane, column block, row, pair) so that each
     // column block's TV rows go out as one contiguous run
-    for (int i = threadIdx.x; i < kTileSlots / kRowPad * TU / 2; i += kGridThreads) {
+    for (int i = threadIdx.x; i < TT * TV * TU / 2; i += kGridThreads) {
         const int pair = i & 1, lr = (i >> 1) % TV, blk = (i / (2 * TV)) % (TU / CB), pl = i / (TU * TV / 2);
         const int lc = blk * CB + 2 * pair;
-        const int cell = (pl * TV + lr) * kRowPad + lc;
+        const int cell = pl * kPlaneStride + lr * kRowPad + lc;
         float4 v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
         float2 *dst = stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np);
         *reinterpret_cast<float4 *>(dst) = v;
@@ -500,6 +623,13 @@ cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis
     return cudaGetLastError();
 }
 
+cudaError_t launch_bound_grid_records(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,
+                                      cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    bound_grid_records_kernel<<<blocks_for(M, 256), 256, 0, s>>>(p->L, uvw, vis, M, p->d_brec, p->d_rec);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s) {
     const int64_t n = p->ntiles + 1;
     cudaError_t e = cudaMemsetAsync(p->d_counts, 0, n * sizeof(uint32_t), s);
@@ -558,11 +688,16 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
     const int chunk_tt0 = chunk * (p->P / TT);
     const uint32_t tile_base = (uint32_t)chunk_tt0 * tiles_per_tt;
     const unsigned nblocks = (unsigned)(planes / TT) * tiles_per_tt;
+    if (nblocks == 0) return cudaSuccess;
 #define WS_GRID_CASE(w)                                                                                       \
-    case w:                                                                                                  \
-        grid3d_kernel<w><<<nblocks, kGridThreads, 0, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets,  \
-                                                          p->d_list, tile_base, chunk_tt0, p->d_stack);        \
-        break;
+    case w: {                                                                                                \
+        const cudaError_t e = cudaFuncSetAttribute(grid3d_kernel<w>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                                   (int)GridSmem<w>::bytes);                                   \
+        if (e != cudaSuccess) return e;                                                                      \
+        grid3d_kernel<w><<<nblocks, kGridThreads, GridSmem<w>::bytes, s>>>(                                   \
+            p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list, tile_base, chunk_tt0, p->d_stack);   \
+        break;                                                                                               \
+    }
     switch (p->L.W) {
         WS_GRID_CASE(1)
         WS_GRID_CASE(2)

@@ -38,8 +38,12 @@ def chi2(plan: Plan, f: torch.Tensor, uvw: torch.Tensor, vis: torch.Tensor, sigm
 
 def cg_image(plan: Plan, uvw: torch.Tensor, vis: torch.Tensor, sigma: float, iters: int = 30, lam: float = 0.0,
              real: bool = True, f0: torch.Tensor | None = None, tol: float = 1e-8):
-    """Least-squares image by conjugate gradients; returns (image, [chi^2 per iteration])."""
+    """Least-squares image by conjugate gradients; returns (image, [chi^2 per iteration]).
+
+    uvw is bound to the plan for the iterations (``Plan.bind``): the tap rule and
+    the tile sort are made once, and every application of A and A^H reuses them."""
     N = plan.N
+    plan.bind(uvw)
     dtype = torch.float32 if real else torch.complex64
     f = torch.zeros(N, N, dtype=dtype, device=vis.device) if f0 is None else f0.clone()
     b = plan.grid(uvw, vis)

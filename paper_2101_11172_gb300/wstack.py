@@ -34,6 +34,7 @@ class Plan:
         self.error_bound = info.error_bound
         self.flags = flags
         self.last_status = _lib.WS_OK
+        self._bound = None             # (uvw tensor, its version when bound)
 
     @property
     def workspace_bytes(self) -> int:
@@ -49,10 +50,30 @@ class Plan:
             raise ValueError(f"{name}: need contiguous {dtype} {tuple(shape)} on {self.device}, "
                              f"got {t.dtype} {tuple(t.shape)} on {t.device}")
 
+    def bind(self, uvw: torch.Tensor | None, stream=None) -> None:
+        """Pre-process and bin ``uvw`` once (``ws_plan_bind_uvw``): later calls with this
+        tensor skip that work.  The plan keeps a reference to the tensor, so its memory
+        stays allocated; an in-place change to it is noticed (through the tensor's
+        version counter) and the set is bound again on the next call.  ``None`` unbinds."""
+        if uvw is None:
+            _lib.ws_plan_bind_uvw(self.handle, 0, 0, self._stream(stream))
+            self._bound = None
+            return
+        self._check(uvw, torch.float64, (uvw.shape[0], 3), "uvw")
+        _lib.ws_plan_bind_uvw(self.handle, uvw.data_ptr(), uvw.shape[0], self._stream(stream))
+        self._bound = (uvw, uvw._version)
+
+    def _refresh_binding(self, uvw: torch.Tensor, stream) -> None:
+        b = self._bound
+        if b is not None and b[0].data_ptr() == uvw.data_ptr() and b[0].shape == uvw.shape \
+                and b[0]._version != b[1]:
+            self.bind(b[0], stream)
+
     def degrid(self, image: torch.Tensor, uvw: torch.Tensor, out: torch.Tensor | None = None,
                stream=None) -> torch.Tensor:
         """Algorithm 6: model image -> visibilities (``ws_degrid``)."""
         M = uvw.shape[0]
+        self._refresh_binding(uvw, stream)
         self._check(image, torch.complex64, (self.N, self.N), "image")
         self._check(uvw, torch.float64, (M, 3), "uvw")
         if out is None:
@@ -66,6 +87,7 @@ class Plan:
              stream=None) -> torch.Tensor:
         """Algorithm 5: visibilities -> dirty image (``ws_grid``)."""
         M = uvw.shape[0]
+        self._refresh_binding(uvw, stream)
         self._check(uvw, torch.float64, (M, 3), "uvw")
         self._check(vis, torch.complex64, (M,), "vis")
         if out is None:
@@ -83,6 +105,7 @@ class Plan:
         return _lib.ws_plan_dropped(self.handle)
 
     def close(self):
+        self._bound = None
         if getattr(self, "handle", None):
             _lib.ws_destroy(self.handle)
             self.handle = None

@@ -57,6 +57,7 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.ws_grid(None, None, None, 0, None, None) == _lib.WS_ERR_ARG
     assert lib.ws_degrid(None, None, None, 0, None, None) == _lib.WS_ERR_ARG
     assert lib.ws_plan_info(None, None) == _lib.WS_ERR_ARG
+    assert lib.ws_plan_bind_uvw(None, None, 0, None) == _lib.WS_ERR_ARG
     assert lib.ws_destroy(None) == _lib.WS_OK
 
 

@@ -67,6 +67,24 @@ def test_error_decreases_with_width():
     assert all(b < 0.5 * a for a, b in zip(Es, Es[1:]))
 
 
+def test_error_falls_with_width_up_to_14_at_large_x0():
+    # Figures 3, 5 and 7: at every x0 each added tap lowers E.  At x0 = 0.4 - 0.45 a fit
+    # started cold settled in poorer local minima for W = 8, 12 and 14 (E rose with W);
+    # the fit followed up from x0 = 1/4 must keep E falling all the way to W = 14.
+    for x0, Ws in ((0.45, range(6, 15)), (0.4, range(10, 15))):
+        Es = [least_misfit(W, x0).E for W in Ws]
+        assert all(b < 0.6 * a for a, b in zip(Es, Es[1:])), (x0, Es)
+
+
+def test_double_precision_at_width_14():
+    # Section 6.3: the improved method reaches double-precision accuracy at W = 14
+    # (x0 = 1/4): E falls through the single-precision range near W = 7 down to a few
+    # FP64 rounding units at W = 14
+    Es = {W: least_misfit(W, 0.25).E for W in (12, 13, 14)}
+    assert Es[12] > Es[13] > Es[14]
+    assert 1e-16 < Es[14] < 1e-14, Es
+
+
 def test_fit_is_a_local_minimum():
     # Any small change of h or of C must raise E (Eq. norm_bound is minimised).
     lm = least_misfit(5, 0.25)
