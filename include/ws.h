@@ -112,6 +112,7 @@ typedef struct {
     double nscale;         /* Eq. n_params */
     double error_bound;    /* E of Eq. norm_bound for (W, x0) from the plan's own fit */
     int64_t workspace_bytes;   /* device bytes the plan currently holds */
+    int32_t tile_rows;     /* grid rows per gridding tile: 32 unless tuned (ws_plan_tune) */
 } ws_plan_info_t;
 
 /* Build a plan.
@@ -184,6 +185,26 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
  * range) are reported by every later call on it, as for an unbound call.
  * Waits for the stream before it returns. */
 ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stream_t stream);
+
+/* Tune the plan's gridding tile.  The visibilities are binned into tiles of
+ * 8 w-planes x tile_rows grid rows x 16 grid columns, for gridding (one CTA
+ * owns a tile) and for degridding (the gather order), and the plane
+ * transforms skip the tiles no footprint touches.  tile_rows = 16, 32 or 64
+ * trades entries per visibility against shared memory per CTA and the
+ * occupancy granularity; the fastest depends on N', W, the data and the GPU.
+ * This call times one ws_grid plus one ws_degrid per candidate on the
+ * caller's data (uvw, vis: M visibilities; image: N x N; device memory, read
+ * only) on `stream`, keeps the fastest, and reports it in *tile_rows (may be
+ * NULL).  With cache_path non-NULL the result is read from, or else written
+ * to, that JSON file under the key "<GPU name>|N'=<N'>|W=<W>" (a cached
+ * entry skips the timing).  ws_plan and ws_batch_create apply the cached
+ * entry for their (N', W) when the environment variable WS_TUNE_CACHE names
+ * the file.  Re-tiling drops a bound visibility set.  The tuning allocates
+ * scratch outputs and synchronises the device; call it at set-up, not in a
+ * loop.  The paper has no counterpart: tile shapes are a property of this
+ * GPU implementation. */
+ws_status ws_plan_tune(ws_plan_t plan, const double *uvw, const void *vis, const void *image, int64_t M,
+                       const char *cache_path, ws_stream_t stream, int32_t *tile_rows);
 
 /* Allocation-free degridding.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory while they run (a

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_ARG", 2: "WS_ERR_UV_RANGE", 3: "WS_ERR_W_
                 4: "WS_ERR_CUDA", 5: "WS_ERR_OOM", 6: "WS_ERR_TIMEOUT"}
 
 # every entry point declared in include/ws.h
-EXPORTS = ("ws_plan", "ws_plan_original", "ws_degrid", "ws_grid", "ws_plan_bind_uvw", "ws_degrid_noalloc",
+EXPORTS = ("ws_plan", "ws_plan_original", "ws_degrid", "ws_grid", "ws_plan_bind_uvw", "ws_plan_tune",
+           "ws_degrid_noalloc",
            "ws_plan_dropped", "ws_plan_info", "ws_plan_stats", "ws_destroy", "ws_batch_create", "ws_batch_grid", "ws_batch_degrid",
            "ws_batch_info", "ws_batch_branches", "ws_batch_destroy", "ws_last_error")
 
@@ -32,7 +33,8 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int32), ("Np", ctypes.c_int32), ("W", ctypes.c_int32),
                 ("Nw", ctypes.c_int32), ("t_lo", ctypes.c_int32), ("planes_per_chunk", ctypes.c_int32),
                 ("x0", ctypes.c_double), ("n0", ctypes.c_double), ("nscale", ctypes.c_double),
-                ("error_bound", ctypes.c_double), ("workspace_bytes", ctypes.c_int64)]
+                ("error_bound", ctypes.c_double), ("workspace_bytes", ctypes.c_int64),
+                ("tile_rows", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -79,6 +81,7 @@ def load(path: str = LIB) -> ctypes.CDLL:
     lib.ws_degrid.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_grid.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_plan_bind_uvw.argtypes = [vp, vp, i64, vp]
+    lib.ws_plan_tune.argtypes = [vp, vp, vp, vp, i64, ctypes.c_char_p, vp, ctypes.POINTER(i32)]
     lib.ws_degrid_noalloc.argtypes = [vp, vp, vp, i64, vp, vp]
     lib.ws_plan_dropped.argtypes = [vp, ctypes.POINTER(i64)]
     lib.ws_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
@@ -138,6 +141,15 @@ def ws_grid(plan: int, uvw_ptr: int, vis_ptr: int, M: int, dirty_ptr: int, strea
 def ws_plan_bind_uvw(plan: int, uvw_ptr: int, M: int, stream: int = 0) -> None:
     """Pre-process and bin a uvw set once for later calls with the same pointer and M (0 unbinds)."""
     _check(load().ws_plan_bind_uvw(plan, uvw_ptr, M, stream))
+
+
+def ws_plan_tune(plan: int, uvw_ptr: int, vis_ptr: int, image_ptr: int, M: int, cache_path: str | None = None,
+                 stream: int = 0) -> int:
+    """Time the gridding tile's row counts on this data, keep the fastest; returns it."""
+    rows = ctypes.c_int32()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(load().ws_plan_tune(plan, uvw_ptr, vis_ptr, image_ptr, M, path, stream, ctypes.byref(rows)))
+    return rows.value
 
 
 def ws_degrid_noalloc(plan: int, image_ptr: int, uvw_ptr: int, M: int, vis_ptr: int, stream: int = 0) -> int:

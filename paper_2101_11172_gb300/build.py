@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libws_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["wstack.cu", "transforms.cu", "transforms_4096.cu", "transforms_2048.cu", "transforms_small.cu",
               "noalloc.cu"]
-CXX_SOURCES = ["plan.cpp", "lmfit.cpp", "batch.cpp"]
+CXX_SOURCES = ["plan.cpp", "lmfit.cpp", "batch.cpp", "tune.cpp"]
 
 
 def cuda_home() -> str:

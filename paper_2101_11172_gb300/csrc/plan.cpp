@@ -233,7 +233,7 @@ bool fft_make_plan(int n, FftPlan *F) {
 // from the occupied tiles and reads and writes its output once per chunk.
 void add_occupied_bytes(ws_plan_s *p, bool grid, int64_t M) {
     const Launch &L = p->L;
-    const double tile_plane = (double)TV * TU * sizeof(float2), strip_plane = (double)L.N * TU * sizeof(float2);
+    const double tile_plane = (double)L.tv * TU * sizeof(float2), strip_plane = (double)L.N * TU * sizeof(float2);
     double t_valid = 0.0, s_valid = 0.0, t_full = 0.0;
     for (int tt = 0; tt < L.ntt; ++tt) {
         const double valid = std::min(TT, L.Nw - tt * TT);
@@ -300,6 +300,52 @@ ws_status finish_call(ws_plan_s *p, cudaStream_t s, bool grid, int64_t M) {
 }
 
 }  // namespace
+
+ws_status set_tile_rows(ws_plan_s *p, int tv) {
+    if ((tv != 16 && tv != 32 && tv != 64) || p->L.Np % tv) {
+        set_error("tile rows must be 16, 32 or 64 and divide N' = " + std::to_string(p->L.Np));
+        return WS_ERR_ARG;
+    }
+    if (tv == p->L.tv) return WS_OK;
+    const int ntv = p->L.Np / tv;
+    const int64_t ntiles = (int64_t)p->L.ntu * ntv * p->L.ntt;
+    if (ntiles + 1 > (int64_t)4096 * 4096) {
+        set_error("too many gridding tiles for " + std::to_string(tv) + " rows per tile");
+        return WS_ERR_ARG;
+    }
+    cudaError_t e = cudaDeviceSynchronize();         // the per-tile tables may be in use
+    if (e != cudaSuccess) return cuda_fail(e, "re-tiling: synchronize");
+    uint32_t **tables32[] = {&p->d_counts, &p->d_offsets, &p->d_boff_g, &p->d_boff_d};
+    uint8_t **tables8[] = {&p->d_tile_occ, &p->d_btile_occ};
+    for (uint32_t **t : tables32) {
+        if (*t) p->bytes -= (p->ntiles + 1) * (int64_t)sizeof(uint32_t);
+        cudaFree(*t);
+        *t = nullptr;
+    }
+    for (uint8_t **t : tables8) {
+        if (*t) p->bytes -= p->ntiles;
+        cudaFree(*t);
+        *t = nullptr;
+    }
+    // the bound set's other buffers are kept; its tables are made again by the next bind
+    cudaFree(p->d_bcol_occ);
+    cudaFree(p->d_bdrop);
+    if (p->d_bcol_occ) p->bytes -= (int64_t)p->L.ntt * p->L.ntu;
+    if (p->d_bdrop) p->bytes -= kCounters * (int64_t)sizeof(unsigned long long);
+    p->d_bcol_occ = nullptr;
+    p->d_bdrop = nullptr;
+    p->b_uvw = nullptr;
+    p->b_M = -1;
+    p->L.tv = tv;
+    p->L.tv_log = tv == 16 ? 4 : (tv == 32 ? 5 : 6);
+    p->L.ntv = ntv;
+    p->ntiles = ntiles;
+    if ((e = dev_alloc(&p->d_counts, (size_t)ntiles + 1, &p->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&p->d_offsets, (size_t)ntiles + 1, &p->bytes)) != cudaSuccess ||
+        (e = dev_alloc(&p->d_tile_occ, (size_t)ntiles, &p->bytes)) != cudaSuccess)
+        return cuda_fail(e, "re-tiling: allocating the per-tile tables");
+    return WS_OK;
+}
 
 // Grow the per-call buffers to hold M visibilities.
 ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid) {
@@ -470,6 +516,8 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     L.t_lo = (int)t_lo;
     L.Nw = (int)(t_hi - t_lo + 1);
     L.ntu = (int)(Np / TU);
+    L.tv = TV;
+    L.tv_log = 5;
     L.ntv = (int)(Np / TV);
     L.ntt = (L.Nw + TT - 1) / TT;
     L.uv_scale = Np * (fov / N);
@@ -608,6 +656,18 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         std::memset(p->h_occ_counts, 0, ((size_t)2 * L.ntt + 1) * sizeof(uint32_t));
     }
 #undef WS_TRY
+    // the tuned tile rows for this (GPU, N', W), when a tuning cache is named
+    if (const char *cache = std::getenv("WS_TUNE_CACHE")) {
+        int tv = 0;
+        // an entry that does not fit this plan (rows not dividing N') is ignored
+        if (tune_lookup(cache, tune_key(dev, (int)Np, W), &tv) && tv != L.tv && Np % tv == 0) {
+            st = set_tile_rows(p, tv);
+            if (st != WS_OK) {
+                release(p);
+                return st;
+            }
+        }
+    }
     *out = p;
     return WS_OK;
 fail:
@@ -932,6 +992,7 @@ ws_status ws_plan_info(ws_plan_t plan, ws_plan_info_t *info) {
     info->nscale = plan->L.nscale;
     info->error_bound = plan->fit.E;
     info->workspace_bytes = plan->bytes;
+    info->tile_rows = plan->L.tv;
     return WS_OK;
 }
 

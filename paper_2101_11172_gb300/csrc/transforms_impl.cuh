@@ -163,7 +163,7 @@ fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
         return __ldcs(blk + (size_t)grid_to_crop(S, half, Np) * CB + b);
     };
     auto store = [&](int b, int S, float2 v) {
-        if (occ[S / TV]) blk[(size_t)S * CB + b] = v;     // only tiles the gather reads
+        if (occ[S >> L.tv_log]) blk[(size_t)S * CB + b] = v;     // only tiles the gather reads
     };
     plane_fft<NP, kPerCta>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
 }
@@ -186,7 +186,7 @@ inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
     __syncthreads();
     // gridding wrote only occupied tiles; every other cell is zero
     auto load = [&](int b, int S) -> float2 {
-        return occ[S / TV] ? __ldcs(blk + (size_t)S * CB + b) : make_float2(0.f, 0.f);
+        return occ[S >> L.tv_log] ? __ldcs(blk + (size_t)S * CB + b) : make_float2(0.f, 0.f);
     };
     // keep the N crop rows, compacted into rows 0..N-1 (all reads precede these writes)
     auto store = [&](int b, int S, float2 v) {

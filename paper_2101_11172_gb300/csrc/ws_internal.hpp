@@ -13,11 +13,15 @@
 
 namespace ws {
 
-// Gridding tile owned by one CTA of the gridding kernel: TT w-planes x TV
-// grid rows (v) x TU grid columns (u).  N' is a multiple of 32, so TU and TV
-// divide it; the plane count is padded to a multiple of TT.
+// Gridding tile owned by one CTA of the gridding kernel: TT w-planes x tv
+// grid rows (v) x TU grid columns (u).  The same tiles bin the visibilities
+// for degridding and mark the stack's occupancy.  tv is a plan parameter
+// (16, 32 or 64 rows; a power of two that divides N', which is a multiple of
+// 32), chosen by the tuner or left at TV; the plane count is padded to a
+// multiple of TT.
 constexpr int TU = 16;
-constexpr int TV = 32;
+constexpr int TV = 32;                 // default rows per tile
+constexpr int kMinTileRows = 16, kMaxTileRows = 64;
 constexpr int TT = 8;
 constexpr int kMaxW = 12;
 constexpr int kMaxDeg = 16;
@@ -46,6 +50,7 @@ struct DeviceTables {
 struct Launch {            // geometry the kernels need
     int N, Np, W, Nw, t_lo;
     int ntu, ntv, ntt;     // tile counts along u, v, t
+    int tv, tv_log;        // grid rows per tile (a power of two) and its log2
     double uv_scale;       // u' = u * uv_scale (= N' * dl)
     double nscale, n0m1;   // w' = w * nscale; n0 - 1
     int fold;              // WS_FLAG_HERMITIAN: w < 0 handled as the conjugate at -(u, v, w)
@@ -134,10 +139,19 @@ constexpr int64_t kMaxVis = ((int64_t)1 << 31) / 12;
 ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
                       uint32_t flags, bool own_stack, int32_t orig_bins = 0);
 ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid);
+// Re-tile a plan with tv grid rows per tile: the per-tile tables are sized
+// anew and a bound visibility set is dropped.  WS_ERR_ARG if tv is not 16, 32
+// or 64 or does not divide N'.
+ws_status set_tile_rows(ws_plan_s *p, int tv);
 ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, float2 *dirty,
                        cudaStream_t s);
 ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, int64_t M, float2 *vis,
                          cudaStream_t s);
+
+// Tuning cache (tune.cpp): key of (GPU, N', W); lookup and store of the tile rows.
+std::string tune_key(int dev, int Np, int W);
+bool tune_lookup(const char *path, const std::string &key, int *tile_rows);
+bool tune_store(const char *path, const std::string &key, int tile_rows, const int *cand, const float *ms, int n);
 
 // Launchers (wstack.cu).
 cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,

@@ -123,7 +123,7 @@ template <bool GRID>
 __device__ __forceinline__ int record_keys(const Launch &L, const VisRec &r, uint32_t *keys) {
     if (r.t0 < 0) return 0;
     if (!GRID) {
-        keys[0] = tile_id(L, r.t0 / TT, r.s0 / TV, r.r0 / TU);
+        keys[0] = tile_id(L, r.t0 / TT, r.s0 >> L.tv_log, r.r0 / TU);
         return 1;
     }
     int tu[2], tv[2];
@@ -131,8 +131,8 @@ __device__ __forceinline__ int record_keys(const Launch &L, const VisRec &r, uin
     int tu_last = wrap_add(r.r0, L.W - 1, L.Np) / TU;
     int nu_ = tu_last != tu[0] ? 2 : 1;
     tu[1] = tu_last;
-    tv[0] = r.s0 / TV;
-    int tv_last = wrap_add(r.s0, L.W - 1, L.Np) / TV;
+    tv[0] = r.s0 >> L.tv_log;
+    int tv_last = wrap_add(r.s0, L.W - 1, L.Np) >> L.tv_log;
     int nv_ = tv_last != tv[0] ? 2 : 1;
     tv[1] = tv_last;
     int tt0 = r.t0 / TT, tt1 = (r.t0 + L.W - 1) / TT;
@@ -288,27 +288,32 @@ __global__ void scan_add_kernel(uint32_t *__restrict__ out, const uint32_t *__re
 constexpr int kGridThreads = 256;
 constexpr int kGridWarps = kGridThreads / 32;
 constexpr int kRowPad = TU + 1;                    // shared row stride (floats)
-// Shared plane stride: 552 = 8 (mod 32), so (17 b + 552 c) mod 32 differs for
-// every b < 7 and c < 4: the (row, plane) pairs of one pass hit distinct banks.
-constexpr int kPlaneStride = TV * kRowPad + 8;
-constexpr int kTileFloats = TT * kPlaneStride;
+// Shared plane stride of a tile of R rows: R 17 + 8, which is 8 (mod 32) for
+// R = 32, 64 and 24 (mod 32) for R = 16; either way (17 b + stride c) mod 32
+// differs for every b < 7 and c < 4, so the (row, plane) pairs of one pass
+// hit distinct banks.
+template <int R>
+__host__ __device__ constexpr int plane_stride() { return R * kRowPad + 8; }
+template <int R>
+__host__ __device__ constexpr int tile_floats() { return TT * plane_stride<R>(); }
 constexpr int kCoefStride = 20;                    // kMaxDeg + 1 coefficients per slot, padded for float4 loads
 static_assert(kMaxDeg + 1 <= kCoefStride && kCoefStride % 4 == 0 && kMaxDeg == 16,
               "the Horner steps below read coefficients 0..16 as five float4");
-static_assert(kTileFloats % 4 == 0, "the tile is cleared in float4 stores");
+static_assert(tile_floats<16>() % 4 == 0 && tile_floats<32>() % 4 == 0 && tile_floats<64>() % 4 == 0,
+              "the tile is cleared in float4 stores");
 static_assert(kMaxW <= 15, "tap counts and first taps are packed in 4 bits");
 constexpr int kGeneral = -1;                       // item shape: the part wraps an axis of a small grid
 constexpr int kChunk = 16;                         // entries a warp stages at a time
 
 // Dynamic shared memory of grid3d<W>: the tile (re, im), the weight table,
 // and per warp the staged chunk (weights, items, values, offsets nu).
-template <int W>
+template <int W, int R>
 struct GridSmem {
     static constexpr int S = 3 * W;                // weight slots per entry: u taps, v taps, w taps
     static constexpr int SP = S | 1;               // entry stride of the staged weights
     static constexpr size_t re = 0;
-    static constexpr size_t im = re + (size_t)kTileFloats * 4;
-    static constexpr size_t coef = im + (size_t)kTileFloats * 4;
+    static constexpr size_t im = re + (size_t)tile_floats<R>() * 4;
+    static constexpr size_t coef = im + (size_t)tile_floats<R>() * 4;
     static constexpr size_t wt = coef + (size_t)S * kCoefStride * 4;
     static constexpr size_t item = wt + (size_t)kGridWarps * kChunk * SP * 4;
     static constexpr size_t val = item + (size_t)kGridWarps * kChunk * 16;
@@ -359,12 +364,13 @@ __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float *w
     }
 }
 
-template <int W>
-__global__ void __launch_bounds__(kGridThreads, 4)
+template <int W, int R>
+__global__ void __launch_bounds__(kGridThreads, R <= 32 ? 4 : 2)
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
               uint32_t tile_base, int chunk_tt0, float2 *__restrict__ stack) {
-    using Sm = GridSmem<W>;
+    using Sm = GridSmem<W, R>;
+    constexpr int kPlaneStride = plane_stride<R>(), kTileFloats = tile_floats<R>();
     constexpr int S = Sm::S, SP = Sm::SP;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t tile = tile_base + blockIdx.x;
@@ -390,7 +396,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     __syncthreads();
     const int Np = L.Np;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u_org = tu * TU, v_org = tv * TV, t_org = tt * TT;
+    const int u_org = tu * TU, v_org = tv * R, t_org = tt * TT;
     float *wts = reinterpret_cast<float *>(smem + Sm::wt) + warp * kChunk * SP;
     int4 *items = reinterpret_cast<int4 *>(smem + Sm::item) + warp * kChunk;
     float2 *vals = reinterpret_cast<float2 *>(smem + Sm::val) + warp * kChunk;
@@ -408,7 +414,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
             const VisRec r = rec[k];
             Span su[2], sv[2];
             const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
-            const int nsv = tile_spans(v_org, r.s0, Np, W, TV, sv[0], sv[1]);
+            const int nsv = tile_spans(v_org, r.s0, Np, W, R, sv[0], sv[1]);
             const int dt = t_org - r.t0;
             const int c0 = max(0, dt), c1 = min(W, dt + TT);
             int4 it;
@@ -464,11 +470,11 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                     add_row<W>(re_base + off, im_base + off, wt + a0, na, V.x * wyz, V.y * wyz);
                 }
             } else {
-                // the part wraps around an axis (N' < W + TV): every span pair, taps one by one
+                // the part wraps around an axis (N' < W + R): every span pair, taps one by one
                 const VisRec r = rec[it.w];
                 Span su[2], sv[2];
                 const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
-                const int nsv = tile_spans(v_org, r.s0, Np, W, TV, sv[0], sv[1]);
+                const int nsv = tile_spans(v_org, r.s0, Np, W, R, sv[0], sv[1]);
                 const int dt = t_org - r.t0;
                 const int c0 = max(0, dt), c1 = min(W, dt + TT);
                 for (int iu = 0; iu < nsu; ++iu)
@@ -491,9 +497,9 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     const size_t plane = (size_t)Np * Np;
     const int p0 = t_org - chunk_tt0 * TT;
     // pairs of cells, ordered (plane, column block, row, pair) so that each
-    // column block's TV rows go out as one contiguous run
-    for (int i = threadIdx.x; i < TT * TV * TU / 2; i += kGridThreads) {
-        const int pair = i & 1, lr = (i >> 1) % TV, blk = (i / (2 * TV)) % (TU / CB), pl = i / (TU * TV / 2);
+    // column block's R rows go out as one contiguous run
+    for (int i = threadIdx.x; i < TT * R * TU / 2; i += kGridThreads) {
+        const int pair = i & 1, lr = (i >> 1) % R, blk = (i / (2 * R)) % (TU / CB), pl = i / (TU * R / 2);
         const int lc = blk * CB + 2 * pair;
         const int cell = pl * kPlaneStride + lr * kRowPad + lc;
         float4 v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
@@ -689,15 +695,19 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
     const uint32_t tile_base = (uint32_t)chunk_tt0 * tiles_per_tt;
     const unsigned nblocks = (unsigned)(planes / TT) * tiles_per_tt;
     if (nblocks == 0) return cudaSuccess;
+    const int R = p->L.tv;
+    auto go = [&](auto kernel, size_t smem) -> cudaError_t {
+        const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kernel<<<nblocks, kGridThreads, smem, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list,
+                                                   tile_base, chunk_tt0, p->d_stack);
+        return cudaGetLastError();
+    };
 #define WS_GRID_CASE(w)                                                                                       \
-    case w: {                                                                                                \
-        const cudaError_t e = cudaFuncSetAttribute(grid3d_kernel<w>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                                   (int)GridSmem<w>::bytes);                                   \
-        if (e != cudaSuccess) return e;                                                                      \
-        grid3d_kernel<w><<<nblocks, kGridThreads, GridSmem<w>::bytes, s>>>(                                   \
-            p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list, tile_base, chunk_tt0, p->d_stack);   \
-        break;                                                                                               \
-    }
+    case w:                                                                                                  \
+        if (R == 16) return go(grid3d_kernel<w, 16>, GridSmem<w, 16>::bytes);                                \
+        if (R == 64) return go(grid3d_kernel<w, 64>, GridSmem<w, 64>::bytes);                                \
+        return go(grid3d_kernel<w, 32>, GridSmem<w, 32>::bytes);
     switch (p->L.W) {
         WS_GRID_CASE(1)
         WS_GRID_CASE(2)

@@ -37,6 +37,22 @@ class Plan:
         self._bound = None             # (uvw tensor, its version when bound)
 
     @property
+    def tile_rows(self) -> int:
+        return _lib.ws_plan_info(self.handle).tile_rows
+
+    def tune(self, uvw: torch.Tensor, vis: torch.Tensor, image: torch.Tensor, cache_path: str | None = None,
+             stream=None) -> int:
+        """``ws_plan_tune``: time the gridding tile's row counts on this data and keep the fastest."""
+        M = uvw.shape[0]
+        self._check(uvw, torch.float64, (M, 3), "uvw")
+        self._check(vis, torch.complex64, (M,), "vis")
+        self._check(image, torch.complex64, (self.N, self.N), "image")
+        rows = _lib.ws_plan_tune(self.handle, uvw.data_ptr(), vis.data_ptr(), image.data_ptr(), M, cache_path,
+                                 self._stream(stream))
+        self._bound = None
+        return rows
+
+    @property
     def workspace_bytes(self) -> int:
         return _lib.ws_plan_info(self.handle).workspace_bytes
 
