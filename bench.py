@@ -398,7 +398,7 @@ class OraclePool:
             shm.unlink()
 
 
-def oracle_vis_cost(pool, rng, few=1000, many=16000):
+def oracle_vis_cost(pool, rng, few=2000, many=60000):
     """Wall seconds per visibility of the parallel oracle: two passes over the same
     dense slabs (the planes where most footprints start) that differ only in how many
     visibilities each slab holds."""
@@ -423,7 +423,7 @@ def oracle_sample_text(pool, c_plane, c_vis, n):
     return (f"per step: {pool.procs} processes, each one slab of {wl.W} of the {pool.g.Nw} w-planes (spread over the "
             f"w-range) with up to 4000 visibilities whose footprints lie in it ({n} in all): {c_plane:.3f} wall s per "
             f"plane; {1e6 * c_vis:.2f} wall us per visibility from two passes over the {pool.procs} densest slabs "
-            f"(1000 and 16000 visibilities each); on {pool.procs} cores, extrapolated to {pool.g.Nw} planes and "
+            f"(2000 and 60000 visibilities each); on {pool.procs} cores, extrapolated to {pool.g.Nw} planes and "
             f"{wl.M} visibilities")
 
 

@@ -66,9 +66,16 @@ enum {
                                       ws_degrid reads only the real part of the image; ws_grid returns
                                       the real dirty image Re(sum_k V_k exp(+2 pi i ...)) with a zero
                                       imaginary part.  The plan's w-range is folded the same way. */
-    WS_FLAG_DIVIDE_BY_N = 1u << 4  /* images are the sky brightness I rather than f = I / n (Section 5.2):
+    WS_FLAG_DIVIDE_BY_N = 1u << 4, /* images are the sky brightness I rather than f = I / n (Section 5.2):
                                       ws_degrid uses I / n and ws_grid returns its dirty image divided
                                       by n, which keeps the two adjoint */
+    WS_FLAG_FP64 = 1u << 5         /* everything in double precision, for measuring the method's error
+                                      where it falls below FP32 rounding (W up to 14, Section 6.3):
+                                      images, visibilities and dirty images are complex128 (interleaved
+                                      double re, im), the weights, w-stack, transforms, screens and sums
+                                      FP64.  Plain per-plane kernels, not tuned for throughput; N' must
+                                      be a power of two <= 4096.  Not for ws_plan_original, batches,
+                                      ws_plan_bind_uvw, ws_plan_tune or ws_degrid_noalloc. */
 };
 
 /* Stages of one call, in execution order (Algorithm 5 / Algorithm 6 steps). */
@@ -119,7 +126,7 @@ typedef struct {
  *   N       image side, a multiple of 8, 16..4096
  *   x0      image cropping parameter, 0 < x0 <= 0.5 (Section 3.3 box); N' is
  *           rounded up, so the effective x0 = N/(2 N') <= x0; N' <= 6144
- *   W       least-misfit kernel width, 1..12
+ *   W       least-misfit kernel width, 1..12 (1..14 with WS_FLAG_FP64)
  *   fov     full field of view in direction cosines (l, m in [-fov/2, fov/2)),
  *           0 < fov and (fov/2)^2 * 2 < 1
  *   w_min, w_max  the w-range (wavelengths) every later call must respect
@@ -271,8 +278,12 @@ typedef struct {
 
 /* Build a batch of n >= 1 instances.
  *   x0, W            as for ws_plan, shared by all instances
- *   branches         1..8 parallel branches, or 0: the first call times the
- *                    call with 1, 2 and 4 branches and keeps the fastest
+ *   branches         1..8 parallel branches, or 0: the first call picks the
+ *                    gridding tile rows (16, 32 or 64) for each image size by
+ *                    timing that size's largest instance (unless the tuning
+ *                    cache named by WS_TUNE_CACHE has them; new results are
+ *                    added to it), then times the call with 1, 2 and 4
+ *                    branches and keeps the fastest
  *   workspace_bytes  device bytes shared by the branches' w-stacks; 0 = the
  *                    smaller of 60% of free memory and what `branches` (or 4)
  *                    whole stacks of the largest instance need.  Each slice

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libws_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["wstack.cu", "transforms.cu", "transforms_4096.cu", "transforms_2048.cu", "transforms_small.cu",
-              "noalloc.cu"]
+              "noalloc.cu", "fp64.cu"]
 CXX_SOURCES = ["plan.cpp", "lmfit.cpp", "batch.cpp", "tune.cpp"]
 
 

@@ -11,13 +11,15 @@
 // into a CUDA graph; later calls with the same data pointers replay the graph
 // (one launch from the host), calls with new pointers capture a new one.
 //
-// K = 0 at creation defers the choice: the first call times the graph for
+// K = 0 at creation defers the choice: the first call picks the gridding
+// tile rows for each image size (tune_tiles), then times the graph for
 // K = 1, 2 and 4 (those whose slices still hold TT planes of the largest
 // instance) and keeps the fastest.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <new>
 #include <numeric>
 #include <string>
@@ -172,11 +174,78 @@ ws_status time_graph(ws_batch_s *b, cudaGraphExec_t exec, float *ms) {
     return e == cudaSuccess ? WS_OK : cuda_fail(e, "ws_batch: timing a branch count");
 }
 
+// Enqueue instance i's call of direction dir (0 grid, 1 degrid) on stream s.
+ws_status enqueue_instance(ws_batch_s *b, int i, int dir, const std::vector<const void *> &ptr, cudaStream_t s) {
+    ws_plan_s *p = b->plans[i];
+    const void *a = ptr[3 * i], *c = ptr[3 * i + 1];
+    void *out = const_cast<void *>(ptr[3 * i + 2]);
+    if (dir == 0)
+        return enqueue_grid(p, static_cast<const double *>(a), static_cast<const float2 *>(c), b->M[i],
+                            static_cast<float2 *>(out), s);
+    return enqueue_degrid(p, static_cast<const float2 *>(a), static_cast<const double *>(c), b->M[i],
+                          static_cast<float2 *>(out), s);
+}
+
+// Tile rows per image size: for every N' in the batch without an entry in the
+// tuning cache (WS_TUNE_CACHE), time this call's direction on the instance of
+// that size with the most visibilities for 16, 32 and 64 rows per tile, and
+// give every instance of that size the fastest (recorded in the cache when one
+// is named).  Runs on the batch's stream with one workspace slice per branch.
+ws_status tune_tiles(ws_batch_s *b, int dir, const std::vector<const void *> &ptr) {
+    const int n = (int)b->plans.size();
+    const char *cache = std::getenv("WS_TUNE_CACHE");
+    std::vector<int> sizes;
+    for (ws_plan_s *p : b->plans)
+        if (std::find(sizes.begin(), sizes.end(), p->L.Np) == sizes.end()) sizes.push_back(p->L.Np);
+    if (!assign(b, 1)) return WS_OK;            // tune() reports the workspace problem
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    cudaError_t e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    ws_status st = e == cudaSuccess ? WS_OK : cuda_fail(e, "ws_batch: timing tile shapes");
+    for (int Np : sizes) {
+        if (st != WS_OK) break;
+        int big = -1;
+        for (int i = 0; i < n; ++i)
+            if (b->plans[i]->L.Np == Np && (big < 0 || b->M[i] > b->M[big])) big = i;
+        const std::string key = tune_key(b->dev, Np, b->plans[big]->L.W);
+        int cached = 0;
+        if (tune_lookup(cache, key, &cached) || b->M[big] == 0) continue;
+        int cand[3], nc = 0;
+        float ms[3] = {0.f, 0.f, 0.f};
+        for (int c : {16, 32, 64})
+            if (Np % c == 0) cand[nc++] = c;
+        for (int k = 0; k < nc && st == WS_OK; ++k) {
+            st = set_tile_rows(b->plans[big], cand[k]);
+            if (st != WS_OK) break;
+            st = enqueue_instance(b, big, dir, ptr, b->origin);          // untimed
+            if (st == WS_OK && (e = cudaEventRecord(t0, b->origin)) != cudaSuccess) st = cuda_fail(e, "ws_batch");
+            if (st == WS_OK) st = enqueue_instance(b, big, dir, ptr, b->origin);
+            if (st == WS_OK && (e = cudaEventRecord(t1, b->origin)) == cudaSuccess &&
+                (e = cudaEventSynchronize(t1)) == cudaSuccess)
+                e = cudaEventElapsedTime(&ms[k], t0, t1);
+            if (st == WS_OK && e != cudaSuccess) st = cuda_fail(e, "ws_batch: timing tile shapes");
+        }
+        if (st != WS_OK) break;
+        int k = 0;
+        for (int j = 1; j < nc; ++j)
+            if (ms[j] < ms[k]) k = j;
+        for (int i = 0; i < n && st == WS_OK; ++i)
+            if (b->plans[i]->L.Np == Np) st = set_tile_rows(b->plans[i], cand[k]);
+        if (st == WS_OK && cache && *cache) tune_store(cache, key, cand[k], cand, ms, nc);
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    b->K = 0;
+    return st;
+}
+
 // Pick K by timing this call's graph for K = 1, 2, 4; leaves the best graph in g.
 ws_status tune(ws_batch_s *b, int dir, const std::vector<const void *> &ptr, Graph &g) {
     float best = 0.f;
     int best_K = 0;
     const int n = (int)b->plans.size();
+    ws_status tst = tune_tiles(b, dir, ptr);
+    if (tst != WS_OK) return tst;
     for (int K : {1, 2, 4}) {
         if (K > n && K > 1) break;
         if (!assign(b, K)) continue;
@@ -273,7 +342,7 @@ ws_status ws_batch_create(ws_batch_t *out, int32_t n, const ws_instance_t *inst,
         return WS_ERR_ARG;
     }
     if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_HERMITIAN | WS_FLAG_DIVIDE_BY_N)) {
-        set_error("ws_batch_create: WS_FLAG_TIMING does not apply to batches");
+        set_error("ws_batch_create: only WS_FLAG_ASYNC, WS_FLAG_NO_Z_OFFSET, WS_FLAG_HERMITIAN and WS_FLAG_DIVIDE_BY_N apply to batches");
         return WS_ERR_ARG;
     }
     for (int32_t i = 0; i < n; ++i)

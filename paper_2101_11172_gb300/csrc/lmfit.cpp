@@ -14,7 +14,8 @@
 // pointwise, h(x) = int Re a dnu / int |a|^2 dnu with a = sum_s c_s(nu)
 // exp(2 pi i (s - nu) x).  Substituting that h leaves a small-residual
 // nonlinear least-squares problem in the Chebyshev coefficients, solved by
-// damped Gauss-Newton with Householder QR and a backtracking line search.
+// Gauss-Newton with Householder QR and a backtracking line search (for large
+// x0 followed up from x0 = 1/4).
 // Evenness C(u) = C(-u) is built in: c_{-s}(nu) = c_s(-nu).
 #include "lmfit.hpp"
 
@@ -228,23 +229,23 @@ double h_series(const LeastMisfitFit &f, double x) {
     return y * b1 - b2 + f.h_cheb[0];
 }
 
-bool fit_least_misfit(int W, double x0, LeastMisfitFit *out, std::string *err) {
-    if (W < 1 || W > 16 || !(x0 > 0.0) || x0 > 0.5) {
-        *err = "least-misfit fit needs 1 <= W <= 16 and 0 < x0 <= 0.5";
-        return false;
-    }
-    const int D = 18, nx = 48, nn = 48;
-    Problem P;
-    build_problem(W, x0, D, nx, nn, &P);
-    const int npar = P.npar;
+namespace {
+
+// Damped Gauss-Newton on the coefficients of one problem, from beta (or, if
+// beta is empty, from the best c for h = 1).  The misfit is unchanged by
+// beta -> alpha beta (h scales as 1 / alpha), so the Jacobian has the null
+// direction beta; one extra row asks the step to be orthogonal to beta,
+// which removes it without damping any other direction.  Each step is
+// halved until E^2 falls.
+bool gauss_newton(const Problem &P, std::vector<double> *beta_io, std::string *err) {
+    const int nx = P.nx, nn = P.nn, npar = P.npar;
     const int m = 2 * nx * nn;
     std::vector<double> sq((size_t)nx * nn);
     for (int q = 0; q < nx; ++q)
         for (int j = 0; j < nn; ++j) sq[(size_t)q * nn + j] = std::sqrt(P.wx[q] * P.wn[j]);
-
-    // Start: best c for h = 1, i.e. minimise sum w |1 - a|^2 (linear in beta).
-    std::vector<double> beta;
-    {
+    std::vector<double> &beta = *beta_io;
+    if (beta.empty()) {
+        // Start: best c for h = 1, i.e. minimise sum w |1 - a|^2 (linear in beta).
         std::vector<double> A((size_t)m * npar), b(m, 0.0);
         for (int p = 0; p < npar; ++p)
             for (size_t e = 0; e < (size_t)nx * nn; ++e) {
@@ -260,7 +261,8 @@ bool fit_least_misfit(int W, double x0, LeastMisfitFit *out, std::string *err) {
     }
     State S, C;
     evaluate(P, beta, &S);
-    std::vector<double> J((size_t)(m + npar) * npar), r(m + npar), step;
+    const int rows = m + 1;
+    std::vector<double> J((size_t)rows * npar), r(rows), step;
     std::vector<double> dR((size_t)npar * nx), dQ((size_t)npar * nx);
     for (int iter = 0; iter < 80; ++iter) {
         // Jacobian of rho = 1 - h a with h = R/Q.
@@ -276,7 +278,7 @@ bool fit_least_misfit(int W, double x0, LeastMisfitFit *out, std::string *err) {
                 dR[(size_t)p * nx + q] = sr;
                 dQ[(size_t)p * nx + q] = sqq;
             }
-        double colmax = 0.0;
+        double colmax = 0.0, bnorm = 0.0;
         for (int p = 0; p < npar; ++p) {
             double cn = 0.0;
             for (int q = 0; q < nx; ++q) {
@@ -285,18 +287,17 @@ bool fit_least_misfit(int W, double x0, LeastMisfitFit *out, std::string *err) {
                 for (int j = 0; j < nn; ++j) {
                     size_t e = (size_t)q * nn + j;
                     cplx v = -(dh * S.a[e] + S.h[q] * P.dA[(size_t)p * nx * nn + e]) * sq[e];
-                    J[(size_t)p * (m + npar) + e] = v.real();
-                    J[(size_t)p * (m + npar) + nx * nn + e] = v.imag();
+                    J[(size_t)p * rows + e] = v.real();
+                    J[(size_t)p * rows + nx * nn + e] = v.imag();
                     cn += std::norm(v);
                 }
             }
             colmax = std::max(colmax, cn);
+            bnorm += beta[p] * beta[p];
         }
-        // Tiny Tikhonov rows remove the scale null direction (E is invariant
-        // under beta -> alpha beta) without biasing the step.
-        double damp = std::sqrt(colmax) * 1e-10;
-        for (int p = 0; p < npar; ++p)
-            for (int k = 0; k < npar; ++k) J[(size_t)p * (m + npar) + m + k] = (p == k) ? damp : 0.0;
+        // the gauge row: sqrt(colmax) beta / |beta| . step = 0
+        bnorm = std::sqrt(bnorm);
+        for (int p = 0; p < npar; ++p) J[(size_t)p * rows + m] = std::sqrt(colmax) * beta[p] / bnorm;
         for (int q = 0; q < nx; ++q)
             for (int j = 0; j < nn; ++j) {
                 size_t e = (size_t)q * nn + j;
@@ -304,8 +305,8 @@ bool fit_least_misfit(int W, double x0, LeastMisfitFit *out, std::string *err) {
                 r[e] = -rho.real();
                 r[nx * nn + e] = -rho.imag();
             }
-        for (int k = 0; k < npar; ++k) r[m + k] = 0.0;
-        if (!householder_lstsq(m + npar, npar, J, r, &step)) break;
+        r[m] = 0.0;
+        if (!householder_lstsq(rows, npar, J, r, &step)) break;
         double lam = 1.0;
         bool improved = false;
         std::vector<double> trial(npar);
@@ -324,6 +325,33 @@ bool fit_least_misfit(int W, double x0, LeastMisfitFit *out, std::string *err) {
         std::swap(S, C);
         if (rel < 1e-9) break;
     }
+    return true;
+}
+
+}  // namespace
+
+bool fit_least_misfit(int W, double x0, LeastMisfitFit *out, std::string *err) {
+    if (W < 1 || W > 16 || !(x0 > 0.0) || x0 > 0.5) {
+        *err = "least-misfit fit needs 1 <= W <= 16 and 0 < x0 <= 0.5";
+        return false;
+    }
+    const int D = 18, nx = 48, nn = 48;
+    // Above x0 = 0.3 the minimiser is followed up from x0 = 1/4 in steps of
+    // 0.05, each fit starting from the last one's coefficients: started cold
+    // at large x0, Gauss-Newton can settle in a much poorer local minimum.
+    std::vector<double> path{x0};
+    if (x0 > 0.3) {
+        path.assign(1, 0.25);
+        while (path.back() + 0.05 < x0 - 1e-12) path.push_back(path.back() + 0.05);
+        path.push_back(x0);
+    }
+    Problem P;
+    std::vector<double> beta;
+    for (double xs : path) {
+        build_problem(W, xs, D, nx, nn, &P);
+        if (!gauss_newton(P, &beta, err)) return false;
+    }
+    const int npar = P.npar;
 
     LeastMisfitFit f;
     f.W = W;

@@ -57,6 +57,10 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
         return WS_ERR_ARG;
     }
     const ws_plan_s *p = plan;
+    if (p->fp64) {
+        set_error("ws_degrid_noalloc: not for FP64 plans");
+        return WS_ERR_ARG;
+    }
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p->dev && cudaSetDevice(p->dev) != cudaSuccess) {

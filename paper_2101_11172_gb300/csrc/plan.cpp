@@ -97,6 +97,13 @@ void release(ws_plan_s *p) {
     cudaFree(p->d_btile_occ);
     cudaFree(p->d_bcol_occ);
     cudaFree(p->d_bdrop);
+    cudaFree(p->d_cheb64);
+    cudaFree(p->d_corr64);
+    cudaFree(p->d_z64);
+    cudaFree(p->d_plane64);
+    cudaFree(p->d_acc64);
+    cudaFree(p->d_tw64);
+    cudaFree(p->d_rec64);
     if (p->h_drop) cudaFreeHost(p->h_drop);
     if (p->h_occ_counts) cudaFreeHost(p->h_occ_counts);
     delete p;
@@ -347,6 +354,21 @@ ws_status set_tile_rows(ws_plan_s *p, int tv) {
     return WS_OK;
 }
 
+// FP64 plans: grow the record buffer to hold M visibilities.
+ws_status ensure_capacity64(ws_plan_s *p, int64_t M) {
+    const int64_t need = std::max<int64_t>(M, 1);
+    if (need <= p->rec64_cap) return WS_OK;
+    cudaFree(p->d_rec64);
+    p->bytes -= p->rec64_cap * (int64_t)fp64_record_bytes();
+    p->rec64_cap = 0;
+    p->d_rec64 = nullptr;
+    cudaError_t e = cudaMalloc(&p->d_rec64, (size_t)need * fp64_record_bytes());
+    if (e != cudaSuccess) return cuda_fail(e, "allocating FP64 visibility records");
+    p->bytes += need * (int64_t)fp64_record_bytes();
+    p->rec64_cap = need;
+    return WS_OK;
+}
+
 // Grow the per-call buffers to hold M visibilities.
 ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid) {
     if (M > p->rec_cap) {
@@ -418,8 +440,13 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         set_error("ws_plan: need 0 < x0 <= 0.5");
         return WS_ERR_ARG;
     }
-    if (W < 1 || W > kMaxW) {
-        set_error("ws_plan: need 1 <= W <= 12");
+    const bool fp64 = (flags & WS_FLAG_FP64) != 0;
+    if (W < 1 || W > (fp64 ? kMaxW64 : kMaxW)) {
+        set_error(fp64 ? "ws_plan: need 1 <= W <= 14 (FP64 plans)" : "ws_plan: need 1 <= W <= 12 (14 with WS_FLAG_FP64)");
+        return WS_ERR_ARG;
+    }
+    if (fp64 && (orig_bins > 0 || !own_stack)) {
+        set_error("ws_plan: WS_FLAG_FP64 is for ws_plan only (not original W-stacking plans or batches)");
         return WS_ERR_ARG;
     }
     const double lmax = 0.5 * fov;
@@ -432,13 +459,17 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         return WS_ERR_ARG;
     }
     if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_TIMING | WS_FLAG_HERMITIAN |
-                            WS_FLAG_DIVIDE_BY_N)) {
+                            WS_FLAG_DIVIDE_BY_N | WS_FLAG_FP64)) {
         set_error("ws_plan: unknown flag bits");
         return WS_ERR_ARG;
     }
     const int64_t Np = fft_size(N, x0);
     if (Np > 6144) {
         set_error("ws_plan: FFT grid N' = N/(2 x0) rounded up must not exceed 6144");
+        return WS_ERR_ARG;
+    }
+    if (fp64 && ((Np & (Np - 1)) != 0 || Np > 4096)) {
+        set_error("ws_plan: FP64 plans need a power-of-two N' <= 4096, got " + std::to_string(Np));
         return WS_ERR_ARG;
     }
     ws_plan_s *p = new (std::nothrow) ws_plan_s;
@@ -564,6 +595,7 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     for (int j = 0; j < N; ++j) hx[j] = h_series(p->fit, (j - N / 2) / (double)Np);
     std::vector<float> corr((size_t)N * N);
     std::vector<float2> zs((size_t)N * N);
+    std::vector<double> corr64(fp64 ? (size_t)N * N : 0), z64(fp64 ? (size_t)N * N : 0);
     for (int i = 0; i < N; ++i) {
         const double m = (i - N / 2) * dl;
         for (int j = 0; j < N; ++j) {
@@ -577,7 +609,12 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
                 corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * inv_n);   // Algorithm 3 step 5: 2-D correction
             } else {
                 z = std::min(std::max(z, -p->x0), p->x0);
-                corr[(size_t)i * N + j] = (float)(hx[i] * hx[j] * h_series(p->fit, z) * inv_n);
+                const double c = hx[i] * hx[j] * h_series(p->fit, z) * inv_n;
+                corr[(size_t)i * N + j] = (float)c;
+                if (fp64) {
+                    corr64[(size_t)i * N + j] = c;
+                    z64[(size_t)i * N + j] = z;
+                }
             }
             const double hi = std::nearbyint(z * 8192.0) / 8192.0;
             zs[(size_t)i * N + j] = make_float2((float)hi, (float)(z - hi));
@@ -599,13 +636,15 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     cudaMemGetInfo(&free_b, &total_b);
     size_t budget = (size_t)(0.6 * (double)free_b);
     if (const char *env = std::getenv("WS_STACK_BYTES")) budget = (size_t)std::strtoull(env, nullptr, 10);
-    int P = L.ntt * TT;
+    int P = fp64 ? 0 : L.ntt * TT;
+    if (fp64) own_stack = false;                  // FP64 plans work one plane at a time
     if (const char *env = std::getenv("WS_PLANES_PER_CHUNK")) {
         int want = std::atoi(env);
         if (want > 0) P = std::min(P, std::max(TT, (want / TT) * TT));
     }
     const int fit_planes = (int)std::min<size_t>(budget / plane_bytes, (size_t)1 << 20);
     if (fit_planes < P) P = std::max(TT, (fit_planes / TT) * TT);
+    if (fp64) P = 0;
     p->P = own_stack ? P : 0;             // a batch hands the plan a shared stack later
 
     ws_status st = WS_OK;
@@ -649,6 +688,34 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     WS_TRY(dev_alloc(&p->d_drop, (size_t)kCounters, &p->bytes), "allocating drop counters");
     WS_TRY(cudaMallocHost((void **)&p->h_drop, kCounters * sizeof(unsigned long long)), "allocating pinned counters");
     std::memset(p->h_drop, 0, kCounters * sizeof(unsigned long long));
+    if (fp64) {
+        p->fp64 = true;
+        const int D = p->fit.degree;
+        std::vector<double> cheb2(p->fit.cheb.begin(), p->fit.cheb.end());
+        cheb2.insert(cheb2.end(), p->fit.cheb.begin(), p->fit.cheb.end());
+        std::vector<double2> tw64((size_t)Np);
+        for (int64_t m = 0; m < Np; ++m) {
+            const double ang = 2.0 * 3.14159265358979323846 * (double)m / (double)Np;
+            tw64[m] = make_double2(std::cos(ang), -std::sin(ang));
+        }
+        (void)D;
+        WS_TRY(dev_alloc(&p->d_cheb64, cheb2.size(), &p->bytes), "allocating FP64 weights");
+        WS_TRY(cudaMemcpy(p->d_cheb64, cheb2.data(), cheb2.size() * sizeof(double), cudaMemcpyHostToDevice),
+               "uploading FP64 weights");
+        WS_TRY(dev_alloc(&p->d_corr64, corr64.size(), &p->bytes), "allocating FP64 correction");
+        WS_TRY(cudaMemcpy(p->d_corr64, corr64.data(), corr64.size() * sizeof(double), cudaMemcpyHostToDevice),
+               "uploading FP64 correction");
+        WS_TRY(dev_alloc(&p->d_z64, z64.size(), &p->bytes), "allocating FP64 z");
+        WS_TRY(cudaMemcpy(p->d_z64, z64.data(), z64.size() * sizeof(double), cudaMemcpyHostToDevice),
+               "uploading FP64 z");
+        WS_TRY(dev_alloc(&p->d_tw64, tw64.size(), &p->bytes), "allocating FP64 twiddles");
+        WS_TRY(cudaMemcpy(p->d_tw64, tw64.data(), tw64.size() * sizeof(double2), cudaMemcpyHostToDevice),
+               "uploading FP64 twiddles");
+        WS_TRY(dev_alloc(&p->d_plane64, (size_t)Np * Np, &p->bytes), "allocating the FP64 plane");
+        WS_TRY(dev_alloc(&p->d_acc64, (size_t)N * N, &p->bytes), "allocating the FP64 accumulator");
+        p->fft64_log = 0;
+        while ((1LL << p->fft64_log) < Np) ++p->fft64_log;
+    }
     if (flags & WS_FLAG_TIMING) {
         WS_TRY(dev_alloc(&p->d_occ_counts, (size_t)2 * L.ntt, &p->bytes), "allocating occupancy counts");
         WS_TRY(cudaMallocHost((void **)&p->h_occ_counts, ((size_t)2 * L.ntt + 1) * sizeof(uint32_t)),
@@ -836,6 +903,13 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
         return WS_ERR_CUDA;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->fp64) {
+        ws_status st = ensure_capacity64(p, M);
+        if (st != WS_OK) return st;
+        st = enqueue_grid64(p, uvw, static_cast<const double2 *>(vis), M, static_cast<double2 *>(dirty), s);
+        if (st != WS_OK) return st;
+        return finish_call(p, s, true, 0);
+    }
     ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), true);
     if (st != WS_OK) return st;
     st = enqueue_grid(p, uvw, static_cast<const float2 *>(vis), M, static_cast<float2 *>(dirty), s);
@@ -856,6 +930,13 @@ ws_status ws_degrid(ws_plan_t plan, const void *image, const double *uvw, int64_
         return WS_ERR_CUDA;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->fp64) {
+        ws_status st = ensure_capacity64(p, M);
+        if (st != WS_OK) return st;
+        st = enqueue_degrid64(p, static_cast<const double2 *>(image), uvw, M, static_cast<double2 *>(vis), s);
+        if (st != WS_OK) return st;
+        return finish_call(p, s, false, 0);
+    }
     ws_status st = ensure_capacity(p, std::max<int64_t>(M, 1), false);
     if (st != WS_OK) return st;
     st = enqueue_degrid(p, static_cast<const float2 *>(image), uvw, M, static_cast<float2 *>(vis), s);
@@ -882,6 +963,10 @@ ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stre
         return WS_ERR_ARG;
     }
     ws_plan_s *p = plan;
+    if (p->fp64) {
+        set_error("ws_plan_bind_uvw: not for FP64 plans");
+        return WS_ERR_ARG;
+    }
     p->b_uvw = nullptr;                      // invalid until the new set is complete
     p->b_M = -1;
     if (!uvw) return WS_OK;

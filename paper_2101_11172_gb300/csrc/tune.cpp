@@ -120,6 +120,10 @@ extern "C" ws_status ws_plan_tune(ws_plan_t plan, const double *uvw, const void 
         return WS_ERR_ARG;
     }
     ws_plan_s *p = plan;
+    if (p->fp64) {
+        set_error("ws_plan_tune: not for FP64 plans");
+        return WS_ERR_ARG;
+    }
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != p->dev && cudaSetDevice(p->dev) != cudaSuccess) {

@@ -24,6 +24,7 @@ constexpr int TV = 32;                 // default rows per tile
 constexpr int kMinTileRows = 16, kMaxTileRows = 64;
 constexpr int TT = 8;
 constexpr int kMaxW = 12;
+constexpr int kMaxW64 = 14;            // widths of FP64 plans (WS_FLAG_FP64)
 constexpr int kMaxDeg = 16;
 // Per-call device counters: visibilities dropped for non-finite u, v; for w
 // outside the plan's range; and bounded device waits that gave up.
@@ -110,6 +111,17 @@ struct ws_plan_s {
     uint8_t *d_btile_occ = nullptr;         // ntiles
     uint8_t *d_bcol_occ = nullptr;          // ntt x ntu
     unsigned long long *d_bdrop = nullptr;  // kCounters: the bound set's drop counts
+    // FP64 plans (WS_FLAG_FP64): their own tables and one plane of workspace
+    bool fp64 = false;
+    double *d_cheb64 = nullptr;             // 2 x W x (degree+1): Chebyshev series of c_i(nu), (u, v) then w
+    double *d_corr64 = nullptr;             // N x N
+    double *d_z64 = nullptr;                // N x N
+    double2 *d_plane64 = nullptr;           // N' x N'
+    double2 *d_acc64 = nullptr;             // N x N
+    double2 *d_tw64 = nullptr;              // N': exp(-2 pi i m / N')
+    int fft64_log = 0;
+    void *d_rec64 = nullptr;
+    int64_t rec64_cap = 0;
     // occupancy statistics (WS_FLAG_TIMING): per t-tile, occupied tiles and
     // (t-tile, u-strip) strips, then the number of tile-list entries
     uint32_t *d_occ_counts = nullptr;       // 2 ntt
@@ -139,6 +151,7 @@ constexpr int64_t kMaxVis = ((int64_t)1 << 31) / 12;
 ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double fov, double w_min, double w_max,
                       uint32_t flags, bool own_stack, int32_t orig_bins = 0);
 ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid);
+ws_status ensure_capacity64(ws_plan_s *p, int64_t M);
 // Re-tile a plan with tv grid rows per tile: the per-tile tables are sized
 // anew and a bound visibility set is dropped.  WS_ERR_ARG if tv is not 16, 32
 // or 64 or does not divide N'.
@@ -152,6 +165,13 @@ ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, i
 std::string tune_key(int dev, int Np, int W);
 bool tune_lookup(const char *path, const std::string &key, int *tile_rows);
 bool tune_store(const char *path, const std::string &key, int tile_rows, const int *cand, const float *ms, int n);
+
+// FP64 path (fp64.cu).
+size_t fp64_record_bytes();
+ws_status enqueue_grid64(ws_plan_s *p, const double *uvw, const double2 *vis, int64_t M, double2 *dirty,
+                         cudaStream_t s);
+ws_status enqueue_degrid64(ws_plan_s *p, const double2 *image, const double *uvw, int64_t M, double2 *vis,
+                           cudaStream_t s);
 
 // Launchers (wstack.cu).
 cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,

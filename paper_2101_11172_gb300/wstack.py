@@ -3,7 +3,8 @@
 Only marshalling happens here (shapes, dtypes, pointers, the current CUDA
 stream); the computation is the CUDA library's.  Tensors must already live on
 the plan's device: complex64 images (N, N) with rows along m and columns along
-l, complex64 visibilities (M,), float64 uvw (M, 3) in wavelengths.
+l, complex64 visibilities (M,), float64 uvw (M, 3) in wavelengths; complex128
+images and visibilities for plans made with WS_FLAG_FP64.
 """
 from __future__ import annotations
 
@@ -33,6 +34,7 @@ class Plan:
         self.x0, self.n0, self.nscale = info.x0, info.n0, info.nscale
         self.error_bound = info.error_bound
         self.flags = flags
+        self.cdtype = torch.complex128 if flags & _lib.WS_FLAG_FP64 else torch.complex64
         self.last_status = _lib.WS_OK
         self._bound = None             # (uvw tensor, its version when bound)
 
@@ -90,11 +92,11 @@ class Plan:
         """Algorithm 6: model image -> visibilities (``ws_degrid``)."""
         M = uvw.shape[0]
         self._refresh_binding(uvw, stream)
-        self._check(image, torch.complex64, (self.N, self.N), "image")
+        self._check(image, self.cdtype, (self.N, self.N), "image")
         self._check(uvw, torch.float64, (M, 3), "uvw")
         if out is None:
-            out = torch.empty(M, dtype=torch.complex64, device=self.device)
-        self._check(out, torch.complex64, (M,), "out")
+            out = torch.empty(M, dtype=self.cdtype, device=self.device)
+        self._check(out, self.cdtype, (M,), "out")
         self.last_status = _lib.ws_degrid(self.handle, image.data_ptr(), uvw.data_ptr(), M,
                                           out.data_ptr(), self._stream(stream))
         return out
@@ -105,10 +107,10 @@ class Plan:
         M = uvw.shape[0]
         self._refresh_binding(uvw, stream)
         self._check(uvw, torch.float64, (M, 3), "uvw")
-        self._check(vis, torch.complex64, (M,), "vis")
+        self._check(vis, self.cdtype, (M,), "vis")
         if out is None:
-            out = torch.empty(self.N, self.N, dtype=torch.complex64, device=self.device)
-        self._check(out, torch.complex64, (self.N, self.N), "out")
+            out = torch.empty(self.N, self.N, dtype=self.cdtype, device=self.device)
+        self._check(out, self.cdtype, (self.N, self.N), "out")
         self.last_status = _lib.ws_grid(self.handle, uvw.data_ptr(), vis.data_ptr(), M,
                                         out.data_ptr(), self._stream(stream))
         return out

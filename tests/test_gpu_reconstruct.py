@@ -1,6 +1,10 @@
 """Least-squares imaging through the CUDA operators: conjugate gradients on chi^2
-for a 34-source real sky drive chi^2 down monotonically to the noise level and
-recover the sources.  The data are exact (the oracle's DFT) plus noise."""
+for the paper's 34-source sky (Appendix A, the field of Sections 6.3 and 7) drive
+chi^2 down monotonically to the noise level and recover the sources.  The data
+are exact (the oracle's DFT) plus noise."""
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -21,14 +25,29 @@ def dev():
     return torch.device("cuda", 0)
 
 
-def test_cg_recovers_a_point_source_sky(dev):
+def appendix_sky(N):
+    """The Appendix A sources on an N x N map of the same 6-degree field: table
+    pixel (X, Y) from the centre, 24 arcseconds each, lands on image pixel
+    (N/2 + round(Y N / 900), N/2 + round(X N / 900)), row along m, column along l."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", "appendix_a_sky.json")) as f:
+        table = json.load(f)
+    sky = np.zeros((N, N))
+    scale = N / table["map_pixels"]
+    for _, X, Y, flux in table["sources"]:
+        sky[N // 2 + int(round(Y * scale)), N // 2 + int(round(X * scale))] += flux
+    fov = np.deg2rad(table["field_deg"])
+    return sky, fov
+
+
+def test_cg_recovers_the_appendix_sky(dev):
     from paper_2101_11172_gb300.reconstruct import cg_image
     from paper_2101_11172_gb300.wstack import Plan
-    N, fov, M, sigma = 64, 0.4, 20000, 0.01
+    N, M, sigma = 128, 60000, 0.01
+    sky, fov = appendix_sky(N)
+    assert np.count_nonzero(sky) == 34 and sky.sum() == 52.0
     rng = synth.rng_for(0, 3000)
     R = 0.45 * N / fov
     uvw = synth.disc_uvw(M, R, 0.05 * R * 20, rng)
-    sky = synth.point_sky(N, 34, rng).real
     g = make_geometry(N, 0.25, 7, fov, float(uvw[:, 2].min()), float(uvw[:, 2].max()))
     rows, cols = np.nonzero(sky)
     vis = dft.dft_degrid(uvw, dft.pixel_lmn(g, rows, cols), sky[rows, cols]) + synth.complex_normal(M, rng, sigma)
@@ -38,7 +57,7 @@ def test_cg_recovers_a_point_source_sky(dev):
         f = f.cpu().numpy().astype(np.float64)
     print("chi^2 / M by iteration:", [round(h / M, 3) for h in hist[::15]])
     assert all(b <= a * (1 + 1e-6) for a, b in zip(hist, hist[1:]))      # CG never raises chi^2 here
-    # down to the noise level: about 1 - 4096 / (2 M) = 0.9 once the 4096 pixels are fitted
+    # down to the noise level: about 1 - N^2 / (2 M) once the pixels are fitted
     assert hist[-1] / M < 1.3 and hist[0] / hist[-1] > 1e4
     # the sources come back: the recovered image correlates with the sky and the
     # 34 brightest recovered pixels are the source pixels

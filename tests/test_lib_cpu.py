@@ -58,6 +58,12 @@ def test_argument_validation_needs_no_device(lib):
     assert lib.ws_degrid(None, None, None, 0, None, None) == _lib.WS_ERR_ARG
     assert lib.ws_plan_info(None, None) == _lib.WS_ERR_ARG
     assert lib.ws_plan_bind_uvw(None, None, 0, None) == _lib.WS_ERR_ARG
+    # FP64 plans: W up to 14, power-of-two N' only, not for the original method
+    assert lib.ws_plan(ctypes.byref(h), 64, 0.25, 15, 0.2, -1, 1, _lib.WS_FLAG_FP64) == _lib.WS_ERR_ARG
+    assert lib.ws_plan(ctypes.byref(h), 200, 0.25, 7, 0.2, -1, 1, _lib.WS_FLAG_FP64) == _lib.WS_ERR_ARG
+    assert "power-of-two" in _lib.ws_last_error()
+    assert lib.ws_plan(ctypes.byref(h), 64, 0.25, 13, 0.2, -1, 1, 0) == _lib.WS_ERR_ARG
+    assert lib.ws_plan_original(ctypes.byref(h), 64, 0.25, 7, 0.2, -1, 1, 20, _lib.WS_FLAG_FP64) == _lib.WS_ERR_ARG
     assert lib.ws_destroy(None) == _lib.WS_OK
 
 
