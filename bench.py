@@ -401,7 +401,9 @@ class OraclePool:
 def oracle_vis_cost(pool, rng, few=2000, many=60000):
     """Wall seconds per visibility of the parallel oracle: two passes over the same
     dense slabs (the planes where most footprints start) that differ only in how many
-    visibilities each slab holds."""
+    visibilities each slab holds, after one untimed pass (the processes' first pass
+    pays for first-touch allocations and transform set-up)."""
+    pool.slab_step(rng, few, dense=True)
     t_few, _, n_few = pool.slab_step(rng, few, dense=True)
     t_many, _, n_many = pool.slab_step(rng, many, dense=True)
     return max(0.0, (t_many - t_few) / (n_many - n_few)) if n_many > n_few else 0.0

@@ -353,12 +353,11 @@ __device__ __forceinline__ void red_shared(unsigned addr, float v) {
 
 // Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a tile row (re and im at byte addresses).
 template <int W, int A = 0>
-__device__ __forceinline__ void add_row(unsigned re, unsigned im, const float *wx, int na, float pr, float pi) {
+__device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[W], int na, float pr, float pi) {
     if constexpr (A < W) {
         if (A < na) {
-            const float w = wx[A];
-            red_shared_at<4 * A>(re, pr * w);
-            red_shared_at<4 * A>(im, pi * w);
+            red_shared_at<4 * A>(re, pr * wx[A]);
+            red_shared_at<4 * A>(im, pi * wx[A]);
             add_row<W, A + 1>(re, im, wx, na, pr, pi);
         }
     }
@@ -462,12 +461,16 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                 const int a0 = (it.y >> 12) & 15, b0 = (it.y >> 16) & 15, cw0 = (it.y >> 20) & 15;
                 const float inv_nb = __int_as_float(it.z);
                 const int nbc = nb * nc;
+                // the part's u-tap weights, all read before the first reduction
+                float wx[W];
+#pragma unroll
+                for (int a = 0; a < W; ++a) wx[a] = a < na ? wt[a0 + a] : 0.f;
                 for (int q = lane; q < nbc; q += 32) {
                     // q = cc nb + bb, q < 144: (q + 1/2) / nb is at least 1/24 from an integer
                     const int cc = __float2int_rz(((float)q + 0.5f) * inv_nb), bb = q - cc * nb;
                     const float wyz = wt[W + b0 + bb] * wt[2 * W + cw0 + cc];
                     const unsigned off = (unsigned)(it.x + cc * kPlaneStride + bb * kRowPad) * 4u;
-                    add_row<W>(re_base + off, im_base + off, wt + a0, na, V.x * wyz, V.y * wyz);
+                    add_row<W>(re_base + off, im_base + off, wx, na, V.x * wyz, V.y * wyz);
                 }
             } else {
                 // the part wraps around an axis (N' < W + R): every span pair, taps one by one
