@@ -227,20 +227,25 @@ def library_source_sha() -> str:
     return h.hexdigest()
 
 
-def traffic_for(stage: str, occupied_bytes_per_launch):
+def traffic_for(stage: str, occupied_bytes_per_launch, planes_per_launch):
     """DRAM bytes of one launch of a stage, scaled from the committed ncu summary
     (profiles/traffic.json: one capture of each kernel on the small profiling
-    workload, DRAM bytes against the same launch's occupied algorithmic bytes).
-    A kernel's DRAM traffic grows in proportion to the occupied tiles and strips
-    it processes, so the capture's ratio times this launch's occupied bytes is
-    the traffic of a full launch.  None if the library's device code changed
-    since the capture, or the stage was not captured."""
+    workload, DRAM bytes beside the same launch's occupied algorithmic bytes and
+    w-planes).  A kernel's DRAM traffic grows in proportion to the occupied tiles and
+    strips it processes, or, for inv_rows' whole-row copies, to its planes; the
+    capture's ratio times this launch's figure is the traffic of a full launch.  None
+    if the library's device code changed since the capture, or the stage was not
+    captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             data = json.load(f)
         ent = data.get("stages", {}).get(stage)
-        if ent and occupied_bytes_per_launch and data.get("source_sha256") == library_source_sha():
+        if not ent or data.get("source_sha256") != library_source_sha():
+            return None
+        if ent.get("scale") == "planes":
+            return int(round(ent["dram_bytes_per_launch"] / ent["planes"] * planes_per_launch))
+        if occupied_bytes_per_launch:
             return int(round(ent["dram_bytes_per_launch"] / ent["occupied_bytes_per_launch"]
                              * occupied_bytes_per_launch))
     except (OSError, ValueError, KeyError, TypeError, ZeroDivisionError):
@@ -790,7 +795,7 @@ def main():
     dom = max(ours, key=lambda k: ours[k]["ms_per_step"])
     d = stages[dom]
     occ_b = None if d["occupied_gb_per_launch"] is None else d["occupied_gb_per_launch"] * 1e9
-    traffic = traffic_for(dom, occ_b)
+    traffic = traffic_for(dom, occ_b, min(plan.Nw, total_planes // nchunks))
     t_s = d["ms_per_launch"] / 1e3
     roof = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
             "frac": None if d["gbs"] is None else d["gbs"] / peak, "peak_source": peak_src,
