@@ -69,13 +69,20 @@ enum {
     WS_FLAG_DIVIDE_BY_N = 1u << 4, /* images are the sky brightness I rather than f = I / n (Section 5.2):
                                       ws_degrid uses I / n and ws_grid returns its dirty image divided
                                       by n, which keeps the two adjoint */
-    WS_FLAG_FP64 = 1u << 5         /* everything in double precision, for measuring the method's error
+    WS_FLAG_FP64 = 1u << 5,        /* everything in double precision, for measuring the method's error
                                       where it falls below FP32 rounding (W up to 14, Section 6.3):
                                       images, visibilities and dirty images are complex128 (interleaved
                                       double re, im), the weights, w-stack, transforms, screens and sums
                                       FP64.  Plain per-plane kernels, not tuned for throughput; N' must
                                       be a power of two <= 4096.  Not for ws_plan_original, batches,
                                       ws_plan_bind_uvw, ws_plan_tune or ws_degrid_noalloc. */
+    WS_FLAG_DETERMINISTIC = 1u << 6 /* bit-for-bit reproducible gridding: each gridding tile sums in 64-bit
+                                      fixed point (a per-tile power-of-two scale keeps every sum below
+                                      2^62, resolution about 1e-19 of the tile's largest possible sum), so
+                                      ws_grid's dirty image does not depend on the order of the
+                                      visibilities or of the GPU's atomics.  Slower gridding (twice the
+                                      shared memory per tile); degridding is deterministic anyway.  For
+                                      the FP32 path (not WS_FLAG_FP64 plans). */
 };
 
 /* Stages of one call, in execution order (Algorithm 5 / Algorithm 6 steps). */

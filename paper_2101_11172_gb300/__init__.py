@@ -4,10 +4,11 @@ The computation lives in the CUDA library ``_build/libws_gb300.so`` behind the
 C ABI of ``include/ws.h``; :mod:`._lib` binds it with ctypes and
 :mod:`.wstack` wraps it for PyTorch device tensors.
 """
-from ._lib import (WS_FLAG_ASYNC, WS_FLAG_DIVIDE_BY_N, WS_FLAG_FP64, WS_FLAG_HERMITIAN, WS_FLAG_NO_Z_OFFSET,  # noqa: F401
-                   WS_FLAG_TIMING, WsError, load)
+from ._lib import (WS_FLAG_ASYNC, WS_FLAG_DETERMINISTIC, WS_FLAG_DIVIDE_BY_N, WS_FLAG_FP64, WS_FLAG_HERMITIAN,  # noqa: F401
+                   WS_FLAG_NO_Z_OFFSET, WS_FLAG_TIMING, WsError, load)
 
-__all__ = ["Plan", "WsError", "load", "WS_FLAG_ASYNC", "WS_FLAG_DIVIDE_BY_N", "WS_FLAG_FP64", "WS_FLAG_HERMITIAN",
+__all__ = ["Plan", "WsError", "load", "WS_FLAG_ASYNC", "WS_FLAG_DETERMINISTIC", "WS_FLAG_DIVIDE_BY_N", "WS_FLAG_FP64",
+           "WS_FLAG_HERMITIAN",
            "WS_FLAG_NO_Z_OFFSET", "WS_FLAG_TIMING"]
 
 

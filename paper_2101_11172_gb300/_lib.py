@@ -19,6 +19,7 @@ WS_FLAG_TIMING = 4
 WS_FLAG_HERMITIAN = 8
 WS_FLAG_DIVIDE_BY_N = 16
 WS_FLAG_FP64 = 32
+WS_FLAG_DETERMINISTIC = 64
 STAGES = ("prep", "bin", "grid3d", "cols_inv", "rows_inv", "correct", "rows_fwd", "cols_fwd", "degrid3d")
 STATUS_NAMES = {0: "WS_OK", 1: "WS_ERR_ARG", 2: "WS_ERR_UV_RANGE", 3: "WS_ERR_W_RANGE",
                 4: "WS_ERR_CUDA", 5: "WS_ERR_OOM", 6: "WS_ERR_TIMEOUT"}

@@ -341,8 +341,10 @@ ws_status ws_batch_create(ws_batch_t *out, int32_t n, const ws_instance_t *inst,
         set_error("ws_batch_create: need n >= 1 instances and 0 <= branches <= 8");
         return WS_ERR_ARG;
     }
-    if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_HERMITIAN | WS_FLAG_DIVIDE_BY_N)) {
-        set_error("ws_batch_create: only WS_FLAG_ASYNC, WS_FLAG_NO_Z_OFFSET, WS_FLAG_HERMITIAN and WS_FLAG_DIVIDE_BY_N apply to batches");
+    if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_HERMITIAN | WS_FLAG_DIVIDE_BY_N |
+                            WS_FLAG_DETERMINISTIC)) {
+        set_error("ws_batch_create: only WS_FLAG_ASYNC, WS_FLAG_NO_Z_OFFSET, WS_FLAG_HERMITIAN, WS_FLAG_DIVIDE_BY_N "
+                  "and WS_FLAG_DETERMINISTIC apply to batches");
         return WS_ERR_ARG;
     }
     for (int32_t i = 0; i < n; ++i)
@@ -366,7 +368,8 @@ ws_status ws_batch_create(ws_batch_t *out, int32_t n, const ws_instance_t *inst,
     for (int32_t i = 0; i < n && st == WS_OK; ++i) {
         ws_plan_s *p = nullptr;
         st = plan_create(&p, inst[i].N, x0, W, inst[i].fov, inst[i].w_min, inst[i].w_max,
-                         flags & (WS_FLAG_NO_Z_OFFSET | WS_FLAG_HERMITIAN | WS_FLAG_DIVIDE_BY_N), false);
+                         flags & (WS_FLAG_NO_Z_OFFSET | WS_FLAG_HERMITIAN | WS_FLAG_DIVIDE_BY_N | WS_FLAG_DETERMINISTIC),
+                         false);
         if (st != WS_OK) {
             set_error("ws_batch_create: instance " + std::to_string(i) + ": " + ws_last_error());
             break;

@@ -459,7 +459,7 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         return WS_ERR_ARG;
     }
     if (flags & ~(uint32_t)(WS_FLAG_ASYNC | WS_FLAG_NO_Z_OFFSET | WS_FLAG_TIMING | WS_FLAG_HERMITIAN |
-                            WS_FLAG_DIVIDE_BY_N | WS_FLAG_FP64)) {
+                            WS_FLAG_DIVIDE_BY_N | WS_FLAG_FP64 | WS_FLAG_DETERMINISTIC)) {
         set_error("ws_plan: unknown flag bits");
         return WS_ERR_ARG;
     }
@@ -588,6 +588,21 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
         p->wcoef_host.insert(p->wcoef_host.end(), mono.begin(), mono.end());
     }
     p->orig_bins = orig_bins;
+    {
+        // |c_i(nu)| at most wmax over the taps of each table (sampled finely; the weights are
+        // smooth), so |C_x C_y C_z| <= wmax_uv^2 wmax_w; 2 % margin for the FP32 evaluation
+        const int D1 = p->wdeg + 1;
+        double wmax[2] = {0.0, 0.0};
+        for (int tab = 0; tab < 2; ++tab)
+            for (int i = 0; i < W; ++i)
+                for (int k = 0; k <= 2048; ++k) {
+                    const double nu = -0.5 + k / 2048.0;
+                    double acc = 0.0;
+                    for (int m = p->wdeg; m >= 0; --m) acc = acc * nu + p->wcoef_host[((size_t)tab * W + i) * D1 + m];
+                    wmax[tab] = std::max(wmax[tab], std::fabs(acc));
+                }
+        p->wbound = (float)(1.02 * wmax[0] * wmax[0] * wmax[1]);
+    }
 
     // correction image h(x_j) h(y_i) h(z_ij) and the split z_ij (Eq. z-on-sphere)
     const double dl = fov / N;

@@ -68,6 +68,7 @@ struct ws_plan_s {
     ws::LeastMisfitFit fit;
     int wdeg = 0;
     std::vector<float> wcoef_host;
+    float wbound = 1.f;            // bound on |C_x C_y C_z| over all taps and offsets (deterministic gridding)
 
     // device tables (plan lifetime)
     float *d_wcoef = nullptr;      // 2 x W x (wdeg+1): taps along u and v, then along w

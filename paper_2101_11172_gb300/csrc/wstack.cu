@@ -305,15 +305,17 @@ static_assert(kMaxW <= 15, "tap counts and first taps are packed in 4 bits");
 constexpr int kGeneral = -1;                       // item shape: the part wraps an axis of a small grid
 constexpr int kChunk = 16;                         // entries a warp stages at a time
 
-// Dynamic shared memory of grid3d<W>: the tile (re, im), the weight table,
-// and per warp the staged chunk (weights, items, values, offsets nu).
-template <int W, int R>
+// Dynamic shared memory of grid3d<W, R, DET>: the tile (re, im; FP32 sums, or
+// 64-bit fixed-point sums for the deterministic mode), the weight table, and
+// per warp the staged chunk (weights, items, values, offsets nu).
+template <int W, int R, bool DET>
 struct GridSmem {
     static constexpr int S = 3 * W;                // weight slots per entry: u taps, v taps, w taps
     static constexpr int SP = S | 1;               // entry stride of the staged weights
+    static constexpr int ES = DET ? 8 : 4;         // bytes per tile cell component
     static constexpr size_t re = 0;
-    static constexpr size_t im = re + (size_t)tile_floats<R>() * 4;
-    static constexpr size_t coef = im + (size_t)tile_floats<R>() * 4;
+    static constexpr size_t im = re + (size_t)tile_floats<R>() * ES;
+    static constexpr size_t coef = im + (size_t)tile_floats<R>() * ES;
     static constexpr size_t wt = coef + (size_t)S * kCoefStride * 4;
     static constexpr size_t item = wt + (size_t)kGridWarps * kChunk * SP * 4;
     static constexpr size_t val = item + (size_t)kGridWarps * kChunk * 16;
@@ -351,27 +353,55 @@ __device__ __forceinline__ void red_shared(unsigned addr, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
+// The deterministic mode's shared-memory add: a contribution v becomes the
+// 64-bit integer nearest v 2^scale, and integer sums do not depend on the
+// order of their terms.
+template <int OFF>
+__device__ __forceinline__ void red_shared_fixed_at(unsigned addr, float v, int scale) {
+    const unsigned long long q = (unsigned long long)__float2ll_rn(ldexpf(v, scale));
+    asm volatile("red.shared.add.u64 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "l"(q) : "memory");
+}
+
+// One contribution to a tile cell component at byte address addr + OFF.
+template <bool DET, int OFF>
+__device__ __forceinline__ void add_cell(unsigned addr, float v, int scale) {
+    if constexpr (DET)
+        red_shared_fixed_at<OFF>(addr, v, scale);
+    else
+        red_shared_at<OFF>(addr, v);
+}
+
 // Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a tile row (re and im at byte addresses).
-template <int W, int A = 0>
-__device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[W], int na, float pr, float pi) {
+template <int W, bool DET, int A = 0>
+__device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[W], int na, float pr, float pi,
+                                        int scale) {
     if constexpr (A < W) {
         if (A < na) {
-            red_shared_at<4 * A>(re, pr * wx[A]);
-            red_shared_at<4 * A>(im, pi * wx[A]);
-            add_row<W, A + 1>(re, im, wx, na, pr, pi);
+            constexpr int ES = DET ? 8 : 4;
+            add_cell<DET, ES * A>(re, pr * wx[A], scale);
+            add_cell<DET, ES * A>(im, pi * wx[A], scale);
+            add_row<W, DET, A + 1>(re, im, wx, na, pr, pi, scale);
         }
     }
 }
 
-template <int W, int R>
-__global__ void __launch_bounds__(kGridThreads, R <= 32 ? 4 : 2)
+// DET: the deterministic mode (WS_FLAG_DETERMINISTIC).  The tile sums in 64-bit
+// fixed point with a per-tile scale 2^scale chosen so that no sum can exceed
+// 2^62: |sum| <= E max|V~| wbound for the tile's E entries, wbound bounding
+// |C_x C_y C_z|.  The scale depends only on the tile's set of entries, and
+// integer additions do not depend on their order, so the tile -- and the dirty
+// image -- come out bit for bit the same whatever order the binning's atomics
+// and the warps' schedule give the entries.
+template <int W, int R, bool DET>
+__global__ void __launch_bounds__(kGridThreads, DET ? 2 : (R <= 32 ? 4 : 2))
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
-              uint32_t tile_base, int chunk_tt0, float2 *__restrict__ stack) {
-    using Sm = GridSmem<W, R>;
-    constexpr int kPlaneStride = plane_stride<R>(), kTileFloats = tile_floats<R>();
+              uint32_t tile_base, int chunk_tt0, float wbound, float2 *__restrict__ stack) {
+    using Sm = GridSmem<W, R, DET>;
+    constexpr int kPlaneStride = plane_stride<R>(), kTileFloats = tile_floats<R>(), ES = Sm::ES;
     constexpr int S = Sm::S, SP = Sm::SP;
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned tile_max;                     // DET: max |V~| of the tile's entries (float bits)
     const uint32_t tile = tile_base + blockIdx.x;
     const uint32_t beg = offsets[tile], end = offsets[tile + 1];
     if (beg == end) return;                           // empty tile: the transforms treat it as zero
@@ -381,9 +411,20 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     const int tu = tile % L.ntu;
     const int tv = (tile / L.ntu) % L.ntv;
     const int tt = tile / (L.ntu * L.ntv);
-    for (int i = threadIdx.x; i < kTileFloats / 4; i += kGridThreads) {
+    for (int i = threadIdx.x; i < kTileFloats * ES / 16; i += kGridThreads) {
         reinterpret_cast<float4 *>(sre)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         reinterpret_cast<float4 *>(sim)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if constexpr (DET) {
+        if (threadIdx.x == 0) tile_max = 0u;
+        __syncthreads();
+        float m = 0.f;
+        for (uint32_t e = beg + threadIdx.x; e < end; e += kGridThreads) {
+            const VisRec r = rec[list[e]];
+            m = fmaxf(m, fmaxf(fabsf(r.vre), fabsf(r.vim)));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&tile_max, __float_as_uint(m));   // non-negative floats order as integers
     }
     // slot l < 3W is (axis l / W, tap l % W); coef holds the (u, v) table and
     // then the w table, W x (deg + 1) each; coefficients past deg are zero
@@ -402,8 +443,18 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     float4 *nus = reinterpret_cast<float4 *>(smem + Sm::nu) + warp * kChunk;
     const unsigned re_base = (unsigned)__cvta_generic_to_shared(sre);
     const unsigned im_base = (unsigned)__cvta_generic_to_shared(sim);
+    const uint32_t E = end - beg;
+    int scale = 0;                                   // DET: sums are kept as integers in units of 2^-scale
+    if constexpr (DET) {
+        const float bound = (float)E * __uint_as_float(tile_max) * wbound;
+        if (bound > 0.f) {
+            int ex;
+            frexpf(bound, &ex);                          // bound < 2^ex
+            scale = 62 - ex;
+        }
+    }
     // this warp's share of the tile's entries
-    const uint32_t E = end - beg, per = (E + kGridWarps - 1) / kGridWarps;
+    const uint32_t per = (E + kGridWarps - 1) / kGridWarps;
     const uint32_t wbeg = beg + min(E, warp * per), wend = beg + min(E, (warp + 1) * per);
     for (uint32_t cbeg = wbeg; cbeg < wend; cbeg += kChunk) {
         const int n = (int)min((uint32_t)kChunk, wend - cbeg);
@@ -469,8 +520,8 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                     // q = cc nb + bb, q < 144: (q + 1/2) / nb is at least 1/24 from an integer
                     const int cc = __float2int_rz(((float)q + 0.5f) * inv_nb), bb = q - cc * nb;
                     const float wyz = wt[W + b0 + bb] * wt[2 * W + cw0 + cc];
-                    const unsigned off = (unsigned)(it.x + cc * kPlaneStride + bb * kRowPad) * 4u;
-                    add_row<W>(re_base + off, im_base + off, wx, na, V.x * wyz, V.y * wyz);
+                    const unsigned off = (unsigned)(it.x + cc * kPlaneStride + bb * kRowPad) * ES;
+                    add_row<W, DET>(re_base + off, im_base + off, wx, na, V.x * wyz, V.y * wyz, scale);
                 }
             } else {
                 // the part wraps around an axis (N' < W + R): every span pair, taps one by one
@@ -487,9 +538,9 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                             const int a = su[iu].a0 + q % na, b = sv[iv].a0 + (q / na) % nb, c = c0 + q / (na * nb);
                             const float w = wt[a] * wt[W + b] * wt[2 * W + c];
                             const unsigned off =
-                                (unsigned)((c - dt) * kPlaneStride + (b - sv[iv].off) * kRowPad + (a - su[iu].off)) * 4u;
-                            red_shared(re_base + off, V.x * w);
-                            red_shared(im_base + off, V.y * w);
+                                (unsigned)((c - dt) * kPlaneStride + (b - sv[iv].off) * kRowPad + (a - su[iu].off)) * ES;
+                            add_cell<DET, 0>(re_base + off, V.x * w, scale);
+                            add_cell<DET, 0>(im_base + off, V.y * w, scale);
                         }
                     }
             }
@@ -505,7 +556,15 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
         const int pair = i & 1, lr = (i >> 1) % R, blk = (i / (2 * R)) % (TU / CB), pl = i / (TU * R / 2);
         const int lc = blk * CB + 2 * pair;
         const int cell = pl * kPlaneStride + lr * kRowPad + lc;
-        float4 v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
+        float4 v;
+        if constexpr (DET) {
+            const long long *qre = reinterpret_cast<const long long *>(sre);
+            const long long *qim = reinterpret_cast<const long long *>(sim);
+            v = make_float4(ldexpf(__ll2float_rn(qre[cell]), -scale), ldexpf(__ll2float_rn(qim[cell]), -scale),
+                            ldexpf(__ll2float_rn(qre[cell + 1]), -scale), ldexpf(__ll2float_rn(qim[cell + 1]), -scale));
+        } else {
+            v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
+        }
         float2 *dst = stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np);
         *reinterpret_cast<float4 *>(dst) = v;
     }
@@ -699,18 +758,24 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
     const unsigned nblocks = (unsigned)(planes / TT) * tiles_per_tt;
     if (nblocks == 0) return cudaSuccess;
     const int R = p->L.tv;
+    const bool det = (p->flags & WS_FLAG_DETERMINISTIC) != 0;
     auto go = [&](auto kernel, size_t smem) -> cudaError_t {
         const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kernel<<<nblocks, kGridThreads, smem, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list,
-                                                   tile_base, chunk_tt0, p->d_stack);
+                                                   tile_base, chunk_tt0, p->wbound, p->d_stack);
         return cudaGetLastError();
     };
 #define WS_GRID_CASE(w)                                                                                       \
     case w:                                                                                                  \
-        if (R == 16) return go(grid3d_kernel<w, 16>, GridSmem<w, 16>::bytes);                                \
-        if (R == 64) return go(grid3d_kernel<w, 64>, GridSmem<w, 64>::bytes);                                \
-        return go(grid3d_kernel<w, 32>, GridSmem<w, 32>::bytes);
+        if (det) {                                                                                           \
+            if (R == 16) return go(grid3d_kernel<w, 16, true>, GridSmem<w, 16, true>::bytes);                \
+            if (R == 64) return go(grid3d_kernel<w, 64, true>, GridSmem<w, 64, true>::bytes);                \
+            return go(grid3d_kernel<w, 32, true>, GridSmem<w, 32, true>::bytes);                             \
+        }                                                                                                    \
+        if (R == 16) return go(grid3d_kernel<w, 16, false>, GridSmem<w, 16, false>::bytes);                  \
+        if (R == 64) return go(grid3d_kernel<w, 64, false>, GridSmem<w, 64, false>::bytes);                  \
+        return go(grid3d_kernel<w, 32, false>, GridSmem<w, 32, false>::bytes);
     switch (p->L.W) {
         WS_GRID_CASE(1)
         WS_GRID_CASE(2)

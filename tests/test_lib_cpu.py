@@ -53,7 +53,7 @@ def test_argument_validation_needs_no_device(lib):
         assert h.value is None
         assert _lib.ws_last_error()
     assert lib.ws_plan(None, 64, 0.25, 7, 0.2, -1, 1, 0) == _lib.WS_ERR_ARG
-    assert lib.ws_plan(ctypes.byref(h), 64, 0.25, 7, 0.2, -1, 1, 1 << 7) == _lib.WS_ERR_ARG
+    assert lib.ws_plan(ctypes.byref(h), 64, 0.25, 7, 0.2, -1, 1, 1 << 8) == _lib.WS_ERR_ARG
     assert lib.ws_grid(None, None, None, 0, None, None) == _lib.WS_ERR_ARG
     assert lib.ws_degrid(None, None, None, 0, None, None) == _lib.WS_ERR_ARG
     assert lib.ws_plan_info(None, None) == _lib.WS_ERR_ARG
