@@ -55,6 +55,8 @@ def parse_args():
                     help="also run the whole workload through the oracle on every core (minutes) and compare "
                          "every GPU output with it")
     ap.add_argument("--no-folded", action="store_true", help="skip the real-sky folded timing")
+    ap.add_argument("--deterministic", action="store_true",
+                    help="bit-for-bit reproducible gridding (WS_FLAG_DETERMINISTIC)")
     ap.add_argument("--real-sky", action="store_true",
                     help="fold w < 0 onto -w (Section 5.4, WS_FLAG_HERMITIAN): real image, real dirty image")
     return ap.parse_args()
@@ -610,7 +612,7 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2101_11172_gb300 import WS_FLAG_HERMITIAN, WS_FLAG_TIMING, _lib
+    from paper_2101_11172_gb300 import WS_FLAG_DETERMINISTIC, WS_FLAG_HERMITIAN, WS_FLAG_TIMING, _lib
     from paper_2101_11172_gb300.wstack import Plan
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -629,6 +631,8 @@ def main():
     wl = load_workload(args.workload)
     M = wl.M
     flags = WS_FLAG_TIMING
+    if args.deterministic:
+        flags |= WS_FLAG_DETERMINISTIC
     if args.real_sky:
         flags |= WS_FLAG_HERMITIAN
         wl.image = wl.image.real.astype(np.complex128)
@@ -847,6 +851,7 @@ def main():
             "config": workload_config(wl, {"grid": plan.Np, "w_planes": plan.Nw,
                                            "planes_per_chunk": plan.planes_per_chunk,
                                            "real_sky_folding": bool(args.real_sky),
+                                           "deterministic_gridding": bool(args.deterministic),
                                            "parallelism": f"replicas x{world}"}),
             "e2e": {"value": replica_value(M, world, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
