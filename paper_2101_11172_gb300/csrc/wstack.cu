@@ -349,6 +349,12 @@ template <int OFF>
 __device__ __forceinline__ void red_shared_at(unsigned addr, float v) {
     asm volatile("red.shared.add.f32 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "f"(v) : "memory");
 }
+// The same, done only where A < n (a predicated instruction, no branch).
+template <int OFF, int A>
+__device__ __forceinline__ void red_shared_at_if(unsigned addr, float v, int n) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.gt.s32 p, %3, %4;\n\t@p red.shared.add.f32 [%0+%1], %2;\n\t}"
+                 ::"r"(addr), "n"(OFF), "f"(v), "r"(n), "n"(A) : "memory");
+}
 __device__ __forceinline__ void red_shared(unsigned addr, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
@@ -372,14 +378,20 @@ __device__ __forceinline__ void add_cell(unsigned addr, float v, int scale) {
 }
 
 // Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a tile row (re and im at byte addresses).
+// The FP32 mode predicates each reduction on a < na instead of branching.
 template <int W, bool DET, int A = 0>
 __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[W], int na, float pr, float pi,
                                         int scale) {
     if constexpr (A < W) {
-        if (A < na) {
-            constexpr int ES = DET ? 8 : 4;
-            add_cell<DET, ES * A>(re, pr * wx[A], scale);
-            add_cell<DET, ES * A>(im, pi * wx[A], scale);
+        if constexpr (DET) {
+            if (A < na) {
+                add_cell<DET, 8 * A>(re, pr * wx[A], scale);
+                add_cell<DET, 8 * A>(im, pi * wx[A], scale);
+                add_row<W, DET, A + 1>(re, im, wx, na, pr, pi, scale);
+            }
+        } else {
+            red_shared_at_if<4 * A, A>(re, pr * wx[A], na);
+            red_shared_at_if<4 * A, A>(im, pi * wx[A], na);
             add_row<W, DET, A + 1>(re, im, wx, na, pr, pi, scale);
         }
     }
@@ -394,7 +406,7 @@ __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&
 // and the warps' schedule give the entries.
 template <int W, int R, bool DET>
 __global__ void __launch_bounds__(kGridThreads, DET ? 2 : (R <= 32 ? 4 : 2))
-grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
+grid3d_kernel(Launch L, const float *__restrict__ wslots, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
               uint32_t tile_base, int chunk_tt0, float wbound, float2 *__restrict__ stack) {
     using Sm = GridSmem<W, R, DET>;
@@ -426,13 +438,9 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((threadIdx.x & 31) == 0) atomicMax(&tile_max, __float_as_uint(m));   // non-negative floats order as integers
     }
-    // slot l < 3W is (axis l / W, tap l % W); coef holds the (u, v) table and
-    // then the w table, W x (deg + 1) each; coefficients past deg are zero
-    for (int i = threadIdx.x; i < S * kCoefStride; i += kGridThreads) {
-        const int l = i / kCoefStride, m = i - l * kCoefStride, axis = l / W, tap = l - axis * W;
-        const int row = (axis == 2 ? W : 0) + tap;
-        scoef[i] = m <= deg ? coef[row * (deg + 1) + m] : 0.f;
-    }
+    // slot l < 3W is (axis l / W, tap l % W): its coefficients of nu^0 .. nu^16, zero-padded to 20
+    for (int i = threadIdx.x; i < S * kCoefStride / 4; i += kGridThreads)
+        reinterpret_cast<float4 *>(scoef)[i] = __ldg(reinterpret_cast<const float4 *>(wslots) + i);
     __syncthreads();
     const int Np = L.Np;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -550,23 +558,27 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     __syncthreads();
     const size_t plane = (size_t)Np * Np;
     const int p0 = t_org - chunk_tt0 * TT;
-    // pairs of cells, ordered (plane, column block, row, pair) so that each
-    // column block's R rows go out as one contiguous run
-    for (int i = threadIdx.x; i < TT * R * TU / 2; i += kGridThreads) {
-        const int pair = i & 1, lr = (i >> 1) % R, blk = (i / (2 * R)) % (TU / CB), pl = i / (TU * R / 2);
-        const int lc = blk * CB + 2 * pair;
+    // one row of a column block (4 cells, two float4) per step, ordered (plane,
+    // column block, row) so that each column block's R rows go out as one contiguous run
+    static_assert(CB == 4, "a step writes the 4 cells of one column-block row");
+    for (int i = threadIdx.x; i < TT * R * (TU / CB); i += kGridThreads) {
+        const int lr = i % R, blk = (i / R) % (TU / CB), pl = i / (R * (TU / CB));
+        const int lc = blk * CB;
         const int cell = pl * kPlaneStride + lr * kRowPad + lc;
-        float4 v;
+        float4 v0, v1;
         if constexpr (DET) {
             const long long *qre = reinterpret_cast<const long long *>(sre);
             const long long *qim = reinterpret_cast<const long long *>(sim);
-            v = make_float4(ldexpf(__ll2float_rn(qre[cell]), -scale), ldexpf(__ll2float_rn(qim[cell]), -scale),
-                            ldexpf(__ll2float_rn(qre[cell + 1]), -scale), ldexpf(__ll2float_rn(qim[cell + 1]), -scale));
+            auto cv = [&](long long q) { return ldexpf(__ll2float_rn(q), -scale); };
+            v0 = make_float4(cv(qre[cell]), cv(qim[cell]), cv(qre[cell + 1]), cv(qim[cell + 1]));
+            v1 = make_float4(cv(qre[cell + 2]), cv(qim[cell + 2]), cv(qre[cell + 3]), cv(qim[cell + 3]));
         } else {
-            v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
+            v0 = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
+            v1 = make_float4(sre[cell + 2], sim[cell + 2], sre[cell + 3], sim[cell + 3]);
         }
-        float2 *dst = stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np);
-        *reinterpret_cast<float4 *>(dst) = v;
+        float4 *dst = reinterpret_cast<float4 *>(stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np));
+        dst[0] = v0;
+        dst[1] = v1;
     }
 }
 
@@ -762,8 +774,8 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
     auto go = [&](auto kernel, size_t smem) -> cudaError_t {
         const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kernel<<<nblocks, kGridThreads, smem, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list,
-                                                   tile_base, chunk_tt0, p->wbound, p->d_stack);
+        kernel<<<nblocks, kGridThreads, smem, s>>>(p->L, p->d_wslots, p->d_rec, p->d_offsets, p->d_list, tile_base,
+                                                   chunk_tt0, p->wbound, p->d_stack);
         return cudaGetLastError();
     };
 #define WS_GRID_CASE(w)                                                                                       \
