@@ -121,6 +121,37 @@ __device__ __forceinline__ void dft<16>(float2 *v, bool inv, const float2 *__res
     for (int i = 0; i < 16; ++i) v[i] = o[i];
 }
 
+// Radix 16 whose middle half of inputs, v[4] .. v[11], is zero (the centred
+// half of a sequence of N' = 2N points zero-padded to N'): the first level's
+// four 4-point DFTs see (a, 0, 0, d) and reduce to two adds and a quarter
+// turn each; v[4..11] need not be set.
+__device__ __forceinline__ void dft16_zero_middle(float2 *v, bool inv) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 a = v[q], d = v[q + 12], rd = rot_q(d, inv);
+        v[q] = cadd(a, d);
+        v[q + 8] = csub(a, d);
+        v[q + 4] = csub(a, rd);
+        v[q + 12] = cadd(a, rd);
+    }
+#pragma unroll
+    for (int q = 1; q < 4; ++q)
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1) v[q + 4 * k1] = cmul(v[q + 4 * k1], w16(q * k1, inv));
+    float2 o[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 a0 = v[0 + 4 * k1], a1 = v[1 + 4 * k1], a2 = v[2 + 4 * k1], a3 = v[3 + 4 * k1];
+        dft4(a0, a1, a2, a3, inv);
+        o[k1] = a0;
+        o[k1 + 4] = a1;
+        o[k1 + 8] = a2;
+        o[k1 + 12] = a3;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = o[i];
+}
+
 // cos and sin of 2 pi m / R for the odd radices R = 3, 5, 7 and 0 <= m < R
 // (decimal expansions of the closed forms; sin is odd in m about R / 2).
 __host__ __device__ constexpr double odd_cos(int R, int m) {
@@ -430,20 +461,32 @@ template <int N> struct Layout {
     __host__ __device__ static constexpr int pad(int e) { return e + (e >> shift); }
 };
 
+// Crop pruning (N' = 2N, the centred half of a sequence is the crop): PRUNE_IN
+// when the inputs outside it are zero, PRUNE_OUT when the outputs outside it
+// are not wanted.  In the first stage, input m (N/R0) + j lies outside it for
+// R0/4 <= m < 3 R0/4; in the last stage, output k + m (N/R) likewise.
+constexpr int PRUNE_IN = 1, PRUNE_OUT = 2;
+
 // First stage (radix R0): inputs m*(N/R0) + j, outputs to digit-reversed g*R0 + m.
-template <int N, int COUNT, class Load>
+template <int N, int COUNT, class Load, int PRUNE = 0>
 __device__ __forceinline__ void first(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
                                       Load &load) {
     using Rd = Radices<N>;
     using Ly = Layout<N>;
     constexpr int R = Rd::r0, nb = N / R, total = COUNT * nb;
+    constexpr bool pin = (PRUNE & PRUNE_IN) != 0;
+    static_assert(!pin || R == 16, "input pruning is written for a radix-16 first stage");
     // j = d1 * r2 + d2 (x-order); g = d1 + d2 * r1 (position order)
     for (int q = tid; q < total; q += nthr) {
         const int t = q % COUNT, j = q / COUNT;
         float2 v[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = load(t, m * nb + j);
-        fftdev::dft<R>(v, inv, tw, N);
+        for (int m = 0; m < R; ++m)
+            if (!pin || m < R / 4 || m >= 3 * R / 4) v[m] = load(t, m * nb + j);
+        if constexpr (pin)
+            fftdev::dft16_zero_middle(v, inv);
+        else
+            fftdev::dft<R>(v, inv, tw, N);
         const int d1 = j >> ilog2(Rd::r2), d2 = j & (Rd::r2 - 1);
         const int g = d1 + d2 * Rd::r1;
         float2 *x = buf + t * Ly::stride + Ly::pad(g * R);     // R divides 2^shift: one base
@@ -468,9 +511,11 @@ __device__ __forceinline__ StageTw stage_twiddles(const float2 *__restrict__ tw,
     return StageTw{fftdev::twiddle(tw, k << lgtw, inv), fftdev::twiddle(tw, (4 * k) << lgtw, inv)};
 }
 
-template <int N, int COUNT, int R, int L, bool LAST, class Store>
+template <int N, int COUNT, int R, int L, bool LAST, class Store, int PRUNE = 0>
 __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
                                       Store &store, const StageTw *pre = nullptr) {
+    constexpr bool pout = LAST && (PRUNE & PRUNE_OUT) != 0;
+    static_assert(!pout || (R % 4 == 0 && R * L == N), "output pruning needs the last stage, R a multiple of 4");
     using Ly = Layout<N>;
     constexpr int nb = N / R, total = COUNT * nb;
     constexpr int lgL = ilog2(L), lgtw = ilog2(N / (R * L));
@@ -505,7 +550,8 @@ __device__ __forceinline__ void later(float2 *buf, const float2 *__restrict__ tw
         fftdev::dft<R>(v, inv, tw, N);
         if constexpr (LAST) {
 #pragma unroll
-            for (int m = 0; m < R; ++m) store(t, base + m * L, v[m]);
+            for (int m = 0; m < R; ++m)
+                if (!pout || m < R / 4 || m >= 3 * R / 4) store(t, base + m * L, v[m]);
         } else {
 #pragma unroll
             for (int m = 0; m < R; ++m) x[at(pbase, base, m)] = v[m];
@@ -551,30 +597,31 @@ __device__ __forceinline__ void first_inplace(float2 *buf, const float2 *__restr
 
 // One transform of the compile-time size N whose input sits in buf in natural
 // order (see first_inplace for live); later stages as in fft_static.
-template <int N, class Between, class Store>
+template <int N, int PRUNE = 0, class Between, class Store>
 __device__ __forceinline__ void fft_static_inplace(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid,
                                                    int nthr, Between between, Store store,
                                                    const fftst::StageTw &s2, const fftst::StageTw &s3,
                                                    uint32_t live = 0xffffffffu) {
     using Rd = fftst::Radices<N>;
     static_assert(Rd::n == 3, "three-stage plans only");
+    static_assert((PRUNE & fftst::PRUNE_IN) == 0, "inputs already in the buffer are not pruned");
     fftst::first_inplace<N>(buf, tw, inv, tid, between, live);
     fftst::later<N, 1, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store, &s2);
-    fftst::later<N, 1, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store, &s3);
+    fftst::later<N, 1, Rd::r2, Rd::r0 * Rd::r1, true, Store, PRUNE>(buf, tw, inv, tid, nthr, store, &s3);
 }
 
 // COUNT transforms of the compile-time size N (see fft_many for the contract).
 // s2, s3: the thread's twiddle bases of stages 2 and 3 (stage_twiddles), for
 // COUNT = 1 callers that transform many sequences; null reads them per call.
-template <int N, int COUNT, class Load, class Store>
+template <int N, int COUNT, int PRUNE = 0, class Load, class Store>
 __device__ __forceinline__ void fft_static(float2 *buf, const float2 *__restrict__ tw, bool inv, int tid, int nthr,
                                            Load load, Store store, const fftst::StageTw *s2 = nullptr,
                                            const fftst::StageTw *s3 = nullptr) {
     using Rd = fftst::Radices<N>;
     static_assert(Rd::n == 3, "three-stage plans only");
-    fftst::first<N, COUNT>(buf, tw, inv, tid, nthr, load);
+    fftst::first<N, COUNT, Load, PRUNE>(buf, tw, inv, tid, nthr, load);
     fftst::later<N, COUNT, Rd::r1, Rd::r0, false>(buf, tw, inv, tid, nthr, store, s2);
-    fftst::later<N, COUNT, Rd::r2, Rd::r0 * Rd::r1, true>(buf, tw, inv, tid, nthr, store, s3);
+    fftst::later<N, COUNT, Rd::r2, Rd::r0 * Rd::r1, true, Store, PRUNE>(buf, tw, inv, tid, nthr, store, s3);
 }
 
 }  // namespace ws

@@ -30,7 +30,10 @@ __host__ __device__ inline bool rows_keep_z(const FftPlan &F, int N) {
 __device__ __forceinline__ int grid_to_crop(int g, int half, int Np) { return g < half ? g + half : g - (Np - half); }
 __device__ __forceinline__ bool in_crop(int g, int half, int Np) { return g < half || g >= Np - half; }
 
-template <int NP, int COUNT, class Load, class Store>
+// PRUNE (fftst::PRUNE_IN / PRUNE_OUT, compile-time plans with N' = 2N only):
+// the inputs outside the centred half are zero / the outputs outside it are
+// not wanted, and the transform skips them.
+template <int NP, int COUNT, int PRUNE = 0, class Load, class Store>
 __device__ __forceinline__ void plane_fft(float2 *buf, const FftPlan &F, const float2 *__restrict__ tw, bool inv,
                                           int tid, int nthr, Load load, Store store) {
     if constexpr (NP == 0)
@@ -38,8 +41,12 @@ __device__ __forceinline__ void plane_fft(float2 *buf, const FftPlan &F, const f
     else if constexpr (NP == 1)
         fft_many<true, COUNT>(buf, F, tw, inv, tid, nthr, load, store);
     else
-        fft_static<NP, COUNT>(buf, tw, inv, tid, nthr, load, store);
+        fft_static<NP, COUNT, PRUNE>(buf, tw, inv, tid, nthr, load, store);
 }
+
+// CROP: N' = 2N on a compile-time plan, so the crop is exactly the centred half.
+template <int NP>
+inline bool crop_half(const Launch &L) { return NP >= 512 && 2 * L.N == L.Np; }
 
 // -- degridding --------------------------------------------------------------
 
@@ -56,7 +63,7 @@ constexpr int kScreenSteps = 8;
 // plane of the CTA's share; on the planes between, the FFT's first stage reads
 // g and leaves g x step in its place for the next plane.  Each pixel is read
 // by the same thread on every plane, so the update needs no barrier.
-template <int NP, bool STEP>
+template <int NP, bool STEP, bool CROP>
 __global__ void __launch_bounds__(kRowThreads, 2)
 fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ img,
                 const float2 *__restrict__ zsplit, const uint8_t *__restrict__ col_occ, int plane0, int planes,
@@ -137,13 +144,13 @@ fwd_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
             if (occ[R / TU]) __stcs(plane + tiled_index(ii, R, Np), v);
         };
         if constexpr (NP >= 512)
-            fft_static<NP, 1>(sbuf, tw, false, tid, kRowThreads, load, store, &s2, &s3);
+            fft_static<NP, 1, CROP ? fftst::PRUNE_IN : 0>(sbuf, tw, false, tid, kRowThreads, load, store, &s2, &s3);
         else
             plane_fft<NP, 1>(sbuf, F, tw, false, tid, kRowThreads, load, store);
     }
 }
 
-template <int NP>
+template <int NP, bool CROP>
 __global__ void __launch_bounds__(kThreads, 2)
 fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_t *__restrict__ tile_occ,
                 const uint8_t *__restrict__ col_occ, int plane0, float2 *__restrict__ stack) {
@@ -165,12 +172,12 @@ fwd_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
     auto store = [&](int b, int S, float2 v) {
         if (occ[S >> L.tv_log]) blk[(size_t)S * CB + b] = v;     // only tiles the gather reads
     };
-    plane_fft<NP, kPerCta>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
+    plane_fft<NP, kPerCta, CROP ? fftst::PRUNE_IN : 0>(sbuf, F, tw, false, threadIdx.x, kThreads, load, store);
 }
 
 // -- gridding ----------------------------------------------------------------
 
-template <int NP>
+template <int NP, bool CROP>
 __global__ void __launch_bounds__(kThreads, 2)
 inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_t *__restrict__ tile_occ,
                 const uint8_t *__restrict__ col_occ, int plane0, float2 *__restrict__ stack) {
@@ -192,7 +199,7 @@ inv_cols_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const uint8_
     auto store = [&](int b, int S, float2 v) {
         if (in_crop(S, half, Np)) blk[(size_t)grid_to_crop(S, half, Np) * CB + b] = v;
     };
-    plane_fft<NP, kPerCta>(sbuf, F, tw, true, threadIdx.x, kThreads, load, store);
+    plane_fft<NP, kPerCta, CROP ? fftst::PRUNE_OUT : 0>(sbuf, F, tw, true, threadIdx.x, kThreads, load, store);
 }
 
 // -- TMA row copies and mbarriers ----------------------------------------------
@@ -255,7 +262,7 @@ struct RowsSmem {
 // footprint touched hold stale data; the first FFT stage masks them to zero.
 // Every wait is bounded; a CTA that gives up counts the failure in *timeouts,
 // waits (bounded) for the copy in flight and returns.
-template <int NP>
+template <int NP, bool CROP>
 __global__ void __launch_bounds__(kRowThreads, 2)
 inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2 *__restrict__ stack,
                 const __grid_constant__ CUtensorMap row_map, const uint8_t *__restrict__ col_occ, int plane0,
@@ -341,7 +348,8 @@ inv_rows_kernel(Launch L, FftPlan F, const float2 *__restrict__ tw, const float2
                 kahan_add(a.y, a.w, v.x * sn + v.y * cs);
                 srow[jj] = a;
             };
-            fft_static_inplace<NP>(row_buf(p), tw, true, tid, kRowThreads, between, store, s2, s3, live);
+            fft_static_inplace<NP, CROP ? fftst::PRUNE_OUT : 0>(row_buf(p), tw, true, tid, kRowThreads, between, store,
+                                                                  s2, s3, live);
         }
         __syncthreads();
         for (int jj = tid; jj < N; jj += kRowThreads) {
@@ -453,33 +461,52 @@ template <int NP>
 struct Transforms {
     static cudaError_t setup(const FftPlan &F, int N) {
         cudaError_t e;
-        if ((e = allow_smem(fwd_rows_kernel<NP, false>, smem_fwd_rows(F, N, false))) != cudaSuccess) return e;
-        if (fwd_rows_step(F, N) && (e = allow_smem(fwd_rows_kernel<NP, true>, smem_fwd_rows(F, N, true))) != cudaSuccess)
+        const bool step = fwd_rows_step(F, N);
+        if ((e = allow_smem(fwd_rows_kernel<NP, false, false>, smem_fwd_rows(F, N, false))) != cudaSuccess) return e;
+        if ((e = allow_smem(fwd_rows_kernel<NP, false, true>, smem_fwd_rows(F, N, false))) != cudaSuccess) return e;
+        if (step && (e = allow_smem(fwd_rows_kernel<NP, true, false>, smem_fwd_rows(F, N, true))) != cudaSuccess)
             return e;
-        if ((e = allow_smem(fwd_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
-        if ((e = allow_smem(inv_cols_kernel<NP>, smem2(F))) != cudaSuccess) return e;
-        return allow_smem(inv_rows_kernel<NP>, smem_inv_rows<NP>(F, N));
+        if (step && (e = allow_smem(fwd_rows_kernel<NP, true, true>, smem_fwd_rows(F, N, true))) != cudaSuccess)
+            return e;
+        if ((e = allow_smem(fwd_cols_kernel<NP, false>, smem2(F))) != cudaSuccess) return e;
+        if ((e = allow_smem(fwd_cols_kernel<NP, true>, smem2(F))) != cudaSuccess) return e;
+        if ((e = allow_smem(inv_cols_kernel<NP, false>, smem2(F))) != cudaSuccess) return e;
+        if ((e = allow_smem(inv_cols_kernel<NP, true>, smem2(F))) != cudaSuccess) return e;
+        if ((e = allow_smem(inv_rows_kernel<NP, false>, smem_inv_rows<NP>(F, N))) != cudaSuccess) return e;
+        return allow_smem(inv_rows_kernel<NP, true>, smem_inv_rows<NP>(F, N));
     }
     static cudaError_t fwd_rows(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
-        const bool step = fwd_rows_step(p->fft, p->L.N);
+        const bool step = fwd_rows_step(p->fft, p->L.N), crop = crop_half<NP>(p->L);
         const dim3 grid(p->L.N, row_groups(p->L.N, planes, p->sms));
         const size_t smem = smem_fwd_rows(p->fft, p->L.N, step);
+        auto go = [&](auto kernel) {
+            kernel<<<grid, kRowThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit, p->d_col_occ,
+                                                   chunk * p->P, planes, p->d_stack);
+        };
         if (step)
-            fwd_rows_kernel<NP, true><<<grid, kRowThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit,
-                                                                      p->d_col_occ, chunk * p->P, planes, p->d_stack);
+            crop ? go(fwd_rows_kernel<NP, true, true>) : go(fwd_rows_kernel<NP, true, false>);
         else
-            fwd_rows_kernel<NP, false><<<grid, kRowThreads, smem, s>>>(p->L, p->fft, p->d_tw, p->d_img, p->d_zsplit,
-                                                                       p->d_col_occ, chunk * p->P, planes, p->d_stack);
+            crop ? go(fwd_rows_kernel<NP, false, true>) : go(fwd_rows_kernel<NP, false, false>);
         return cudaGetLastError();
     }
     static cudaError_t fwd_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
-        fwd_cols_kernel<NP><<<dim3(p->L.Np / kPerCta, planes), kThreads, smem2(p->fft), s>>>(
-            p->L, p->fft, p->d_tw, p->d_tile_occ, p->d_col_occ, chunk * p->P, p->d_stack);
+        const dim3 grid(p->L.Np / kPerCta, planes);
+        if (crop_half<NP>(p->L))
+            fwd_cols_kernel<NP, true><<<grid, kThreads, smem2(p->fft), s>>>(p->L, p->fft, p->d_tw, p->d_tile_occ,
+                                                                         p->d_col_occ, chunk * p->P, p->d_stack);
+        else
+            fwd_cols_kernel<NP, false><<<grid, kThreads, smem2(p->fft), s>>>(p->L, p->fft, p->d_tw, p->d_tile_occ,
+                                                                          p->d_col_occ, chunk * p->P, p->d_stack);
         return cudaGetLastError();
     }
     static cudaError_t inv_cols(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
-        inv_cols_kernel<NP><<<dim3(p->L.Np / kPerCta, planes), kThreads, smem2(p->fft), s>>>(
-            p->L, p->fft, p->d_tw, p->d_tile_occ, p->d_col_occ, chunk * p->P, p->d_stack);
+        const dim3 grid(p->L.Np / kPerCta, planes);
+        if (crop_half<NP>(p->L))
+            inv_cols_kernel<NP, true><<<grid, kThreads, smem2(p->fft), s>>>(p->L, p->fft, p->d_tw, p->d_tile_occ,
+                                                                         p->d_col_occ, chunk * p->P, p->d_stack);
+        else
+            inv_cols_kernel<NP, false><<<grid, kThreads, smem2(p->fft), s>>>(p->L, p->fft, p->d_tw, p->d_tile_occ,
+                                                                          p->d_col_occ, chunk * p->P, p->d_stack);
         return cudaGetLastError();
     }
     static cudaError_t inv_rows(const ws_plan_s *p, int chunk, int planes, bool first, bool last, float2 *dirty,
@@ -489,9 +516,12 @@ struct Transforms {
             const cudaError_t e = row_tensor_map(p, &map);
             if (e != cudaSuccess) return e;
         }
-        inv_rows_kernel<NP><<<p->L.N, kRowThreads, smem_inv_rows<NP>(p->fft, p->L.N), s>>>(
-            p->L, p->fft, p->d_tw, p->d_stack, map, p->d_col_occ, chunk * p->P, planes, p->d_zsplit, p->d_corr,
-            p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty, p->d_drop + 2, p->wait_polls);
+        auto go = [&](auto kernel) {
+            kernel<<<p->L.N, kRowThreads, smem_inv_rows<NP>(p->fft, p->L.N), s>>>(
+                p->L, p->fft, p->d_tw, p->d_stack, map, p->d_col_occ, chunk * p->P, planes, p->d_zsplit, p->d_corr,
+                p->d_acc, first ? 1 : 0, last ? 1 : 0, dirty, p->d_drop + 2, p->wait_polls);
+        };
+        crop_half<NP>(p->L) ? go(inv_rows_kernel<NP, true>) : go(inv_rows_kernel<NP, false>);
         return cudaGetLastError();
     }
 };

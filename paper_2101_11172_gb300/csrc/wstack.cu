@@ -349,12 +349,6 @@ template <int OFF>
 __device__ __forceinline__ void red_shared_at(unsigned addr, float v) {
     asm volatile("red.shared.add.f32 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "f"(v) : "memory");
 }
-// The same, done only where A < n (a predicated instruction, no branch).
-template <int OFF, int A>
-__device__ __forceinline__ void red_shared_at_if(unsigned addr, float v, int n) {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.gt.s32 p, %3, %4;\n\t@p red.shared.add.f32 [%0+%1], %2;\n\t}"
-                 ::"r"(addr), "n"(OFF), "f"(v), "r"(n), "n"(A) : "memory");
-}
 __device__ __forceinline__ void red_shared(unsigned addr, float v) {
     asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
@@ -378,20 +372,14 @@ __device__ __forceinline__ void add_cell(unsigned addr, float v, int scale) {
 }
 
 // Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a tile row (re and im at byte addresses).
-// The FP32 mode predicates each reduction on a < na instead of branching.
 template <int W, bool DET, int A = 0>
 __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[W], int na, float pr, float pi,
                                         int scale) {
     if constexpr (A < W) {
-        if constexpr (DET) {
-            if (A < na) {
-                add_cell<DET, 8 * A>(re, pr * wx[A], scale);
-                add_cell<DET, 8 * A>(im, pi * wx[A], scale);
-                add_row<W, DET, A + 1>(re, im, wx, na, pr, pi, scale);
-            }
-        } else {
-            red_shared_at_if<4 * A, A>(re, pr * wx[A], na);
-            red_shared_at_if<4 * A, A>(im, pi * wx[A], na);
+        if (A < na) {
+            constexpr int ES = DET ? 8 : 4;
+            add_cell<DET, ES * A>(re, pr * wx[A], scale);
+            add_cell<DET, ES * A>(im, pi * wx[A], scale);
             add_row<W, DET, A + 1>(re, im, wx, na, pr, pi, scale);
         }
     }
