@@ -115,7 +115,6 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
     v.L = p->L;
     v.wdeg = p->wdeg;
     v.d_wcoef = p->d_wcoef;
-    v.d_wslots = p->d_wslots;
     v.d_corr = p->d_corr;
     v.d_zsplit = p->d_zsplit;
     v.d_tw = p->d_tw;

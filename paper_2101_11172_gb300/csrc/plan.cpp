@@ -74,7 +74,6 @@ void release(ws_plan_s *p) {
     }
     for (cudaEvent_t e : p->free_events) cudaEventDestroy(e);
     cudaFree(p->d_wcoef);
-    cudaFree(p->d_wslots);
     cudaFree(p->d_corr);
     cudaFree(p->d_zsplit);
     cudaFree(p->d_stack);
@@ -673,18 +672,6 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
             goto fail;                 \
         }                              \
     } while (0)
-    {
-        // slot l < 3W: axis l / W (u, v from the first table, w from the second), tap l % W
-        const int D1 = p->wdeg + 1;
-        std::vector<float> slots((size_t)3 * W * 20, 0.f);
-        for (int l = 0; l < 3 * W; ++l) {
-            const int axis = l / W, tap = l % W, row = (axis == 2 ? W : 0) + tap;
-            for (int m = 0; m < D1 && m < 20; ++m) slots[(size_t)l * 20 + m] = p->wcoef_host[(size_t)row * D1 + m];
-        }
-        WS_TRY(dev_alloc(&p->d_wslots, slots.size(), &p->bytes), "allocating weight slots");
-        WS_TRY(cudaMemcpy(p->d_wslots, slots.data(), slots.size() * sizeof(float), cudaMemcpyHostToDevice),
-               "uploading weight slots");
-    }
     WS_TRY(dev_alloc(&p->d_wcoef, p->wcoef_host.size(), &p->bytes), "allocating weight table");
     WS_TRY(cudaMemcpy(p->d_wcoef, p->wcoef_host.data(), p->wcoef_host.size() * sizeof(float),
                       cudaMemcpyHostToDevice), "uploading weight table");

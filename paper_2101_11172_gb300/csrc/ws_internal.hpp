@@ -72,8 +72,6 @@ struct ws_plan_s {
 
     // device tables (plan lifetime)
     float *d_wcoef = nullptr;      // 2 x W x (wdeg+1): taps along u and v, then along w
-    float *d_wslots = nullptr;     // 3W x 20: the gridding kernel's weight slots (u taps, v taps, w taps),
-                                   // coefficients of nu^0 .. nu^16 zero-padded to 20
     int orig_bins = 0;             // > 0: original W-stacking with this many w-bins
     float *d_corr = nullptr;       // N x N: h(x_j) h(y_i) h(z_ij)
     float2 *d_zsplit = nullptr;    // N x N: z = hi + lo, hi a multiple of 2^-13

@@ -394,7 +394,7 @@ __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&
 // and the warps' schedule give the entries.
 template <int W, int R, bool DET>
 __global__ void __launch_bounds__(kGridThreads, DET ? 2 : (R <= 32 ? 4 : 2))
-grid3d_kernel(Launch L, const float *__restrict__ wslots, const VisRec *__restrict__ rec,
+grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
               uint32_t tile_base, int chunk_tt0, float wbound, float2 *__restrict__ stack) {
     using Sm = GridSmem<W, R, DET>;
@@ -426,9 +426,13 @@ grid3d_kernel(Launch L, const float *__restrict__ wslots, const VisRec *__restri
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((threadIdx.x & 31) == 0) atomicMax(&tile_max, __float_as_uint(m));   // non-negative floats order as integers
     }
-    // slot l < 3W is (axis l / W, tap l % W): its coefficients of nu^0 .. nu^16, zero-padded to 20
-    for (int i = threadIdx.x; i < S * kCoefStride / 4; i += kGridThreads)
-        reinterpret_cast<float4 *>(scoef)[i] = __ldg(reinterpret_cast<const float4 *>(wslots) + i);
+    // slot l < 3W is (axis l / W, tap l % W); coef holds the (u, v) table and
+    // then the w table, W x (deg + 1) each; coefficients past deg are zero
+    for (int i = threadIdx.x; i < S * kCoefStride; i += kGridThreads) {
+        const int l = i / kCoefStride, m = i - l * kCoefStride, axis = l / W, tap = l - axis * W;
+        const int row = (axis == 2 ? W : 0) + tap;
+        scoef[i] = m <= deg ? coef[row * (deg + 1) + m] : 0.f;
+    }
     __syncthreads();
     const int Np = L.Np;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -546,27 +550,23 @@ grid3d_kernel(Launch L, const float *__restrict__ wslots, const VisRec *__restri
     __syncthreads();
     const size_t plane = (size_t)Np * Np;
     const int p0 = t_org - chunk_tt0 * TT;
-    // one row of a column block (4 cells, two float4) per step, ordered (plane,
-    // column block, row) so that each column block's R rows go out as one contiguous run
-    static_assert(CB == 4, "a step writes the 4 cells of one column-block row");
-    for (int i = threadIdx.x; i < TT * R * (TU / CB); i += kGridThreads) {
-        const int lr = i % R, blk = (i / R) % (TU / CB), pl = i / (R * (TU / CB));
-        const int lc = blk * CB;
+    // pairs of cells, ordered (plane, column block, row, pair) so that each
+    // column block's R rows go out as one contiguous run
+    for (int i = threadIdx.x; i < TT * R * TU / 2; i += kGridThreads) {
+        const int pair = i & 1, lr = (i >> 1) % R, blk = (i / (2 * R)) % (TU / CB), pl = i / (TU * R / 2);
+        const int lc = blk * CB + 2 * pair;
         const int cell = pl * kPlaneStride + lr * kRowPad + lc;
-        float4 v0, v1;
+        float4 v;
         if constexpr (DET) {
             const long long *qre = reinterpret_cast<const long long *>(sre);
             const long long *qim = reinterpret_cast<const long long *>(sim);
-            auto cv = [&](long long q) { return ldexpf(__ll2float_rn(q), -scale); };
-            v0 = make_float4(cv(qre[cell]), cv(qim[cell]), cv(qre[cell + 1]), cv(qim[cell + 1]));
-            v1 = make_float4(cv(qre[cell + 2]), cv(qim[cell + 2]), cv(qre[cell + 3]), cv(qim[cell + 3]));
+            v = make_float4(ldexpf(__ll2float_rn(qre[cell]), -scale), ldexpf(__ll2float_rn(qim[cell]), -scale),
+                            ldexpf(__ll2float_rn(qre[cell + 1]), -scale), ldexpf(__ll2float_rn(qim[cell + 1]), -scale));
         } else {
-            v0 = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
-            v1 = make_float4(sre[cell + 2], sim[cell + 2], sre[cell + 3], sim[cell + 3]);
+            v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
         }
-        float4 *dst = reinterpret_cast<float4 *>(stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np));
-        dst[0] = v0;
-        dst[1] = v1;
+        float2 *dst = stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np);
+        *reinterpret_cast<float4 *>(dst) = v;
     }
 }
 
@@ -762,8 +762,8 @@ cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStr
     auto go = [&](auto kernel, size_t smem) -> cudaError_t {
         const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kernel<<<nblocks, kGridThreads, smem, s>>>(p->L, p->d_wslots, p->d_rec, p->d_offsets, p->d_list, tile_base,
-                                                   chunk_tt0, p->wbound, p->d_stack);
+        kernel<<<nblocks, kGridThreads, smem, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list,
+                                                   tile_base, chunk_tt0, p->wbound, p->d_stack);
         return cudaGetLastError();
     };
 #define WS_GRID_CASE(w)                                                                                       \
