@@ -73,8 +73,9 @@ enum {
                                       where it falls below FP32 rounding (W up to 14, Section 6.3):
                                       images, visibilities and dirty images are complex128 (interleaved
                                       double re, im), the weights, w-stack, transforms, screens and sums
-                                      FP64.  Plain per-plane kernels, not tuned for throughput; N' must
-                                      be a power of two <= 4096.  Not for ws_plan_original, batches,
+                                      FP64.  Plain per-plane kernels, not tuned for throughput (their
+                                      gridding sums with FP64 atomics, so it is reproducible to FP64
+                                      rounding, not bit for bit); N' must be a power of two <= 4096.  Not for ws_plan_original, batches,
                                       ws_plan_bind_uvw, ws_plan_tune or ws_degrid_noalloc. */
     WS_FLAG_DETERMINISTIC = 1u << 6 /* bit-for-bit reproducible gridding: each gridding tile sums in 64-bit
                                       fixed point (a per-tile power-of-two scale keeps every sum below
