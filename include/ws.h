@@ -127,7 +127,7 @@ typedef struct {
     double nscale;         /* Eq. n_params */
     double error_bound;    /* E of Eq. norm_bound for (W, x0) from the plan's own fit */
     int64_t workspace_bytes;   /* device bytes the plan currently holds */
-    int32_t tile_rows;     /* grid rows per gridding tile: 32 unless tuned (ws_plan_tune) */
+    int32_t tile_rows;     /* grid rows per gridding tile: 16 unless tuned (ws_plan_tune) */
 } ws_plan_info_t;
 
 /* Build a plan.
@@ -201,11 +201,11 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
  * Waits for the stream before it returns. */
 ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stream_t stream);
 
-/* Tune the plan's gridding tile.  The visibilities are binned into tiles of
- * 8 w-planes x tile_rows grid rows x 16 grid columns, for gridding (one CTA
- * owns a tile) and for degridding (the gather order), and the plane
- * transforms skip the tiles no footprint touches.  tile_rows = 16, 32 or 64
- * trades entries per visibility against shared memory per CTA and the
+/* Tune the plan's gridding tile.  The stack is tiled in 8 w-planes x
+ * tile_rows grid rows x 16 grid columns: gridding gives one CTA each column of
+ * tiles, degridding bins the visibilities by tile (the gather order), and the
+ * plane transforms skip the tiles no footprint touches.  tile_rows = 16, 32
+ * or 64 trades entries per visibility against shared memory per CTA and the
  * occupancy granularity; the fastest depends on N', W, the data and the GPU.
  * This call times one ws_grid plus one ws_degrid per candidate on the
  * caller's data (uvw, vis: M visibilities; image: N x N; device memory, read

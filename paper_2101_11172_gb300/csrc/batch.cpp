@@ -213,7 +213,7 @@ ws_status tune_tiles(ws_batch_s *b, int dir, const std::vector<const void *> &pt
         int cand[3], nc = 0;
         float ms[3] = {0.f, 0.f, 0.f};
         for (int c : {16, 32, 64})
-            if (Np % c == 0) cand[nc++] = c;
+            if (tile_rows_fit(b->plans[big], c)) cand[nc++] = c;
         for (int k = 0; k < nc && st == WS_OK; ++k) {
             st = set_tile_rows(b->plans[big], cand[k]);
             if (st != WS_OK) break;

@@ -143,8 +143,6 @@ extern "C" ws_status ws_degrid_noalloc(ws_plan_t plan, const void *image, const 
             return cuda_fail(e, "ws_degrid_noalloc: prep kernel");
         if ((e = launch_bin(&v, M, false, s)) != cudaSuccess)
             return cuda_fail(e, "ws_degrid_noalloc: binning kernels");
-        if ((e = launch_mark(&v, M, s)) != cudaSuccess)
-            return cuda_fail(e, "ws_degrid_noalloc: occupancy kernel");
         if ((e = launch_correct_image(&v, static_cast<const float2 *>(image), s)) != cudaSuccess)
             return cuda_fail(e, "ws_degrid_noalloc: correction kernel");
         const int nchunks = (total + P - 1) / P;

@@ -308,9 +308,15 @@ ws_status finish_call(ws_plan_s *p, cudaStream_t s, bool grid, int64_t M) {
 
 }  // namespace
 
+bool tile_rows_fit(const ws_plan_s *p, int tv) {
+    return (tv == 16 || tv == 32 || tv == 64) && p->L.Np % tv == 0 &&
+           grid_smem_bytes(p->L.W, tv, (p->flags & WS_FLAG_DETERMINISTIC) != 0) <= kMaxGridSmem;
+}
+
 ws_status set_tile_rows(ws_plan_s *p, int tv) {
-    if ((tv != 16 && tv != 32 && tv != 64) || p->L.Np % tv) {
-        set_error("tile rows must be 16, 32 or 64 and divide N' = " + std::to_string(p->L.Np));
+    if (!tile_rows_fit(p, tv)) {
+        set_error("tile rows must be 16, 32 or 64, divide N' = " + std::to_string(p->L.Np) +
+                  " and give a gridding ring that fits in shared memory (W = " + std::to_string(p->L.W) + ")");
         return WS_ERR_ARG;
     }
     if (tv == p->L.tv) return WS_OK;
@@ -379,8 +385,8 @@ ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid) {
         if (e != cudaSuccess) return cuda_fail(e, "allocating visibility records");
         p->rec_cap = M;
     }
-    // gridding: at most (2 x 2 x ceil((W-1)/TT + 1)) tiles per visibility
-    const int64_t per = grid ? 4 * ((p->L.W - 1 + TT - 1) / TT + 1) : 1;
+    // gridding: at most 2 x 2 tile columns per visibility
+    const int64_t per = grid ? 4 : 1;
     const int64_t need = M * per;
     if (need > p->list_cap) {
         cudaFree(p->d_list);
@@ -547,9 +553,10 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     L.t_lo = (int)t_lo;
     L.Nw = (int)(t_hi - t_lo + 1);
     L.ntu = (int)(Np / TU);
-    L.tv = TV;
-    L.tv_log = 5;
-    L.ntv = (int)(Np / TV);
+    // TV rows per tile, or 16 where a TV-row gridding ring would not fit in shared memory
+    L.tv = grid_smem_bytes(W, TV, (flags & WS_FLAG_DETERMINISTIC) != 0) <= kMaxGridSmem ? TV : 16;
+    L.tv_log = L.tv == 16 ? 4 : (L.tv == 32 ? 5 : 6);
+    L.ntv = (int)(Np / L.tv);
     L.ntt = (L.Nw + TT - 1) / TT;
     L.uv_scale = Np * (fov / N);
     L.nscale = nscale;
@@ -741,8 +748,8 @@ ws_status plan_create(ws_plan_s **out, int32_t N, double x0, int32_t W, double f
     // the tuned tile rows for this (GPU, N', W), when a tuning cache is named
     if (const char *cache = std::getenv("WS_TUNE_CACHE")) {
         int tv = 0;
-        // an entry that does not fit this plan (rows not dividing N') is ignored
-        if (tune_lookup(cache, tune_key(dev, (int)Np, W), &tv) && tv != L.tv && Np % tv == 0) {
+        // an entry that does not fit this plan (rows not dividing N', a ring too large) is ignored
+        if (tune_lookup(cache, tune_key(dev, (int)Np, W), &tv) && tv != L.tv && tile_rows_fit(p, tv)) {
             st = set_tile_rows(p, tv);
             if (st != WS_OK) {
                 release(p);
@@ -815,7 +822,6 @@ ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64
         }
         StageTimer t(p, s, WS_STAGE_BIN, (M > 0 ? 6 : 3) + ((p->flags & WS_FLAG_TIMING) ? 1 : 0));
         if ((e = launch_bin(p, M, true, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: binning kernels");
-        if ((e = launch_mark_grid(p, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy kernel");
     }
     BoundView view(p, bound, true);
     if ((e = copy_occ_counts(p, s)) != cudaSuccess) return cuda_fail(e, "ws_grid: occupancy statistics");
@@ -865,9 +871,8 @@ ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, i
             if ((e = launch_prep(p, uvw, nullptr, M, false, s)) != cudaSuccess)
                 return cuda_fail(e, "ws_degrid: prep kernel");
         }
-        StageTimer t(p, s, WS_STAGE_BIN, 7 + ((p->flags & WS_FLAG_TIMING) ? 1 : 0));
+        StageTimer t(p, s, WS_STAGE_BIN, 6 + ((p->flags & WS_FLAG_TIMING) ? 1 : 0));
         if ((e = launch_bin(p, M, false, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: binning kernels");
-        if ((e = launch_mark(p, M, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy kernel");
     }
     BoundView view(p, bound, false);
     if ((e = copy_occ_counts(p, s)) != cudaSuccess) return cuda_fail(e, "ws_degrid: occupancy statistics");
@@ -991,7 +996,7 @@ ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stre
         return WS_ERR_CUDA;
     }
     const int64_t Mc = std::max<int64_t>(M, 1);
-    const int64_t per = 4 * ((p->L.W - 1 + TT - 1) / TT + 1);     // footprint tiles per visibility, at most
+    const int64_t per = 4;                                         // tile columns per visibility, at most
     cudaError_t e = cudaSuccess;
     auto grow = [&](auto **ptr, int64_t *cap, int64_t need, const char *what) -> bool {
         if (need <= *cap) return true;
@@ -1045,7 +1050,6 @@ ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stre
         p->d_col_occ = p->d_bcol_occ;
         e = launch_prep(p, uvw, nullptr, M, false, s);
         if (e == cudaSuccess) e = launch_bin(p, M, true, s);
-        if (e == cudaSuccess) e = launch_mark_grid(p, s);
         p->d_list = p->d_blist_d;
         p->d_offsets = p->d_boff_d;
         if (e == cudaSuccess) e = launch_bin(p, M, false, s);

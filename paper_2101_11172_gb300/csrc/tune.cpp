@@ -138,14 +138,14 @@ extern "C" ws_status ws_plan_tune(ws_plan_t plan, const double *uvw, const void 
     } restore{prev, p->dev};
     const std::string key = tune_key(p->dev, p->L.Np, p->L.W);
     int best = 0;
-    if (tune_lookup(cache_path, key, &best)) {
+    if (tune_lookup(cache_path, key, &best) && tile_rows_fit(p, best)) {
         const ws_status st = set_tile_rows(p, best);
         if (st == WS_OK && tile_rows) *tile_rows = best;
         return st;
     }
     int cand[3], n = 0;
     for (int c : {16, 32, 64})
-        if (p->L.Np % c == 0) cand[n++] = c;
+        if (tile_rows_fit(p, c)) cand[n++] = c;
     float ms[3] = {0.f, 0.f, 0.f};
     float2 *dirty = nullptr, *vout = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

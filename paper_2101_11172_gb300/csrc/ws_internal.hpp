@@ -13,19 +13,54 @@
 
 namespace ws {
 
-// Gridding tile owned by one CTA of the gridding kernel: TT w-planes x tv
-// grid rows (v) x TU grid columns (u).  The same tiles bin the visibilities
-// for degridding and mark the stack's occupancy.  tv is a plan parameter
-// (16, 32 or 64 rows; a power of two that divides N', which is a multiple of
-// 32), chosen by the tuner or left at TV; the plane count is padded to a
-// multiple of TT.
+#ifdef __CUDACC__
+#define WS_HD __host__ __device__
+#else
+#define WS_HD
+#endif
+
+// Tiles of the stack: TT w-planes x tv grid rows (v) x TU grid columns (u).
+// They bin the visibilities for degridding, mark the stack's occupancy for
+// the plane transforms, and a tile column (all t-tiles of one (v, u) tile) is
+// what one CTA of the gridding kernel owns.  tv is a plan parameter (16, 32 or
+// 64 rows; a power of two that divides N', which is a multiple of 32, and
+// whose gridding ring fits in shared memory), chosen by the tuner or left at
+// TV; the plane count is padded to a multiple of TT.
 constexpr int TU = 16;
-constexpr int TV = 32;                 // default rows per tile
+constexpr int TV = 16;                 // default rows per tile
 constexpr int kMinTileRows = 16, kMaxTileRows = 64;
 constexpr int TT = 8;
 constexpr int kMaxW = 12;
 constexpr int kMaxW64 = 14;            // widths of FP64 plans (WS_FLAG_FP64)
 constexpr int kMaxDeg = 16;
+
+// Gridding kernel shape: 256 threads; each warp stages kChunk entries at a
+// time.  Shared memory holds a ring of TT + W - 1 w-planes of the tile column
+// (rows padded to TU + 1 floats, planes to tv (TU + 1) + 8 floats; re and im,
+// FP32 or, deterministic, 64-bit fixed point), the weight table (3W slots of
+// kCoefStride coefficients) and the warps' staged chunks.
+constexpr int kGridThreads = 256;
+constexpr int kGridWarps = kGridThreads / 32;
+constexpr int kChunk = 16;
+constexpr int kRowPad = TU + 1;
+constexpr int kCoefStride = 20;
+constexpr size_t kMaxGridSmem = 227 * 1024;     // dynamic shared memory of one CTA
+constexpr size_t kSmemPerSM = 228 * 1024;
+WS_HD constexpr int ring_planes(int W) { return TT + W - 1; }
+WS_HD constexpr int plane_stride(int rows) { return rows * kRowPad + 8; }
+WS_HD constexpr size_t grid_smem_bytes(int W, int rows, bool det) {
+    return (size_t)2 * ring_planes(W) * plane_stride(rows) * (det ? 8 : 4)      // ring, re and im
+           + (size_t)3 * W * kCoefStride * 4                                      // weight table
+           + (size_t)kGridWarps * kChunk * ((3 * W) | 1) * 4                      // staged weights
+           + (size_t)kGridWarps * kChunk * (16 + 8 + 16);                         // items, values, nu
+}
+// CTAs of the gridding kernel that fit on one SM (1 KB reserved per CTA), at most 4
+WS_HD constexpr int grid_ctas_per_sm(int W, int rows, bool det) {
+    return (int)(kSmemPerSM / (grid_smem_bytes(W, rows, det) + 1024)) < 1 ? 1
+           : (int)(kSmemPerSM / (grid_smem_bytes(W, rows, det) + 1024)) > 4
+               ? 4
+               : (int)(kSmemPerSM / (grid_smem_bytes(W, rows, det) + 1024));
+}
 // Per-call device counters: visibilities dropped for non-finite u, v; for w
 // outside the plan's range; and bounded device waits that gave up.
 constexpr int kCounters = 3;
@@ -103,7 +138,7 @@ struct ws_plan_s {
     int64_t b_M = -1;
     ws::VisRec *d_brec = nullptr;
     int64_t brec_cap = 0;
-    uint32_t *d_blist_g = nullptr;          // gridding: (visibility, footprint tile) pairs by tile
+    uint32_t *d_blist_g = nullptr;          // gridding: (visibility, tile column) pairs by column and first-tap t-tile
     int64_t blist_g_cap = 0;
     uint32_t *d_blist_d = nullptr;          // degridding: visibilities by first-tap tile
     int64_t blist_d_cap = 0;
@@ -155,8 +190,10 @@ ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid);
 ws_status ensure_capacity64(ws_plan_s *p, int64_t M);
 // Re-tile a plan with tv grid rows per tile: the per-tile tables are sized
 // anew and a bound visibility set is dropped.  WS_ERR_ARG if tv is not 16, 32
-// or 64 or does not divide N'.
+// or 64, does not divide N', or gives a gridding ring larger than shared memory.
 ws_status set_tile_rows(ws_plan_s *p, int tv);
+// Whether tv rows per tile suit the plan (the conditions of set_tile_rows).
+bool tile_rows_fit(const ws_plan_s *p, int tv);
 ws_status enqueue_grid(ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, float2 *dirty,
                        cudaStream_t s);
 ws_status enqueue_degrid(ws_plan_s *p, const float2 *image, const double *uvw, int64_t M, float2 *vis,
@@ -179,9 +216,9 @@ cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis
                         bool grid, cudaStream_t s);
 cudaError_t launch_bound_grid_records(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M,
                                       cudaStream_t s);
+// Binning (gridding: by tile column and first-tap t-tile; degridding: by
+// first-tap tile) and the stack's occupancy maps, from the records d_rec.
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s);
-cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s);
-cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s);
 cudaError_t launch_occ_count(const ws_plan_s *p, cudaStream_t s);
 cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s);
 cudaError_t launch_correct_image(const ws_plan_s *p, const float2 *image, cudaStream_t s);

@@ -112,13 +112,31 @@ __global__ void bound_grid_records_kernel(Launch L, const double *__restrict__ u
 }
 
 // ---------------------------------------------------------------------------
-// Binning: counting sort of (visibility, tile) pairs by tile id
+// Binning: counting sort of (visibility, bin) pairs by bin id
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t tile_id(const Launch &L, int tt, int tv, int tu) {
     return ((uint32_t)tt * L.ntv + tv) * L.ntu + tu;
 }
 
-// Tiles of the gridding footprint (grid) or the tile of the first tap (degrid).
+// Gridding bin: a tile column (tv, tu) and the t-tile of the first tap.  A
+// column's bins are contiguous, in t order.
+__device__ __forceinline__ uint32_t column_bin(const Launch &L, int tv, int tu, int tt) {
+    return ((uint32_t)tv * L.ntu + tu) * L.ntt + tt;
+}
+
+// The tile columns a footprint's W x W taps in (u, v) touch: 1 or 2 along each axis.
+__device__ __forceinline__ void footprint_columns(const Launch &L, const VisRec &r, int *tu, int &nu_, int *tv,
+                                                  int &nv_) {
+    tu[0] = r.r0 / TU;
+    tu[1] = wrap_add(r.r0, L.W - 1, L.Np) / TU;
+    nu_ = tu[1] != tu[0] ? 2 : 1;
+    tv[0] = r.s0 >> L.tv_log;
+    tv[1] = wrap_add(r.s0, L.W - 1, L.Np) >> L.tv_log;
+    nv_ = tv[1] != tv[0] ? 2 : 1;
+}
+
+// Bins of a record: its tile columns with the first tap's t-tile (grid), or
+// the tile of its first tap (degrid).
 template <bool GRID>
 __device__ __forceinline__ int record_keys(const Launch &L, const VisRec &r, uint32_t *keys) {
     if (r.t0 < 0) return 0;
@@ -126,33 +144,35 @@ __device__ __forceinline__ int record_keys(const Launch &L, const VisRec &r, uin
         keys[0] = tile_id(L, r.t0 / TT, r.s0 >> L.tv_log, r.r0 / TU);
         return 1;
     }
-    int tu[2], tv[2];
-    tu[0] = r.r0 / TU;
-    int tu_last = wrap_add(r.r0, L.W - 1, L.Np) / TU;
-    int nu_ = tu_last != tu[0] ? 2 : 1;
-    tu[1] = tu_last;
-    tv[0] = r.s0 >> L.tv_log;
-    int tv_last = wrap_add(r.s0, L.W - 1, L.Np) >> L.tv_log;
-    int nv_ = tv_last != tv[0] ? 2 : 1;
-    tv[1] = tv_last;
-    int tt0 = r.t0 / TT, tt1 = (r.t0 + L.W - 1) / TT;
+    int tu[2], tv[2], nu_, nv_;
+    footprint_columns(L, r, tu, nu_, tv, nv_);
     int n = 0;
-    for (int tt = tt0; tt <= tt1; ++tt)
-        for (int b = 0; b < nv_; ++b)
-            for (int a = 0; a < nu_; ++a) keys[n++] = tile_id(L, tt, tv[b], tu[a]);
+    for (int b = 0; b < nv_; ++b)
+        for (int a = 0; a < nu_; ++a) keys[n++] = column_bin(L, tv[b], tu[a], r.t0 / TT);
     return n;
 }
 
-constexpr int kMaxKeys = 2 * 2 * 3;
+constexpr int kMaxKeys = 2 * 2;
 
+// Counts the record's bins and marks the stack tiles its footprint touches.
+// Every other cell of the stack is zero when gridding and never read when
+// degridding, so the plane kernels skip it.
 template <bool GRID>
-__global__ void count_kernel(Launch L, const VisRec *__restrict__ rec, int64_t M,
-                             uint32_t *__restrict__ counts) {
+__global__ void count_kernel(Launch L, const VisRec *__restrict__ rec, int64_t M, uint32_t *__restrict__ counts,
+                             uint8_t *__restrict__ tile_occ) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= M) return;
+    const VisRec r = rec[k];
     uint32_t keys[kMaxKeys];
-    int n = record_keys<GRID>(L, rec[k], keys);
+    const int n = record_keys<GRID>(L, r, keys);
     for (int i = 0; i < n; ++i) atomicAdd(&counts[keys[i]], 1u);
+    if (n == 0) return;
+    int tu[2], tv[2], nu_, nv_;
+    footprint_columns(L, r, tu, nu_, tv, nv_);
+    const int tt1 = (r.t0 + L.W - 1) / TT;
+    for (int tt = r.t0 / TT; tt <= tt1; ++tt)
+        for (int b = 0; b < nv_; ++b)
+            for (int a = 0; a < nu_; ++a) tile_occ[tile_id(L, tt, tv[b], tu[a])] = 1;   // stores only: no waits
 }
 
 template <bool GRID>
@@ -166,23 +186,13 @@ __global__ void scatter_kernel(Launch L, const VisRec *__restrict__ rec, int64_t
     for (int i = 0; i < n; ++i) list[offsets[keys[i]] + atomicAdd(&fill[keys[i]], 1u)] = (uint32_t)k;
 }
 
-// Occupancy of the stack: which gridding tiles, and which (t-tile, u-tile)
-// strips of N' rows, any visibility footprint touches.  Every other cell of
-// the stack is zero when gridding and never read when degridding, so the
-// plane kernels skip it.  A tile is touched exactly when some (visibility,
-// tile) pair of a footprint names it: gridding reads that from its tile
-// lists (offsets), degridding from a count of the pairs (counts).
-template <bool FROM_COUNTS>
-__global__ void occ_kernel(Launch L, const uint32_t *__restrict__ per_tile, int64_t ntiles,
-                           uint8_t *__restrict__ tile_occ, uint8_t *__restrict__ col_occ) {
+// Occupancy of the (t-tile, u-tile) strips of N' rows: any tile of the strip touched.
+__global__ void strip_occ_kernel(Launch L, const uint8_t *__restrict__ tile_occ, int64_t ntiles,
+                                 uint8_t *__restrict__ col_occ) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntiles) return;
-    const bool occ = FROM_COUNTS ? per_tile[t] != 0 : per_tile[t + 1] != per_tile[t];
-    tile_occ[t] = occ ? 1 : 0;
-    if (occ) {
-        const int64_t c = (t / ((int64_t)L.ntu * L.ntv)) * L.ntu + t % L.ntu;
-        if (!col_occ[c]) col_occ[c] = 1;
-    }
+    if (t >= ntiles || !tile_occ[t]) return;
+    const int64_t c = (t / ((int64_t)L.ntu * L.ntv)) * L.ntu + t % L.ntu;
+    if (!col_occ[c]) col_occ[c] = 1;
 }
 
 // Statistics only (WS_FLAG_TIMING): occupied tiles and occupied (t-tile,
@@ -268,14 +278,21 @@ __global__ void scan_add_kernel(uint32_t *__restrict__ out, const uint32_t *__re
 
 // ---------------------------------------------------------------------------
 // Gridding: Algorithm 5 steps 2 and 3a (Eq. gridded_vis).  One CTA owns one
-// TT x TV x TU tile of the stack chunk, accumulates every (visibility, tile)
-// pair of its list in shared memory and writes the tile exactly once.
+// tile column -- TU grid columns x tv grid rows through every w-plane of the
+// plane chunk -- and walks the column's bins in t order.  A bin holds the
+// visibilities whose first tap lies in one t-tile, so their footprints reach
+// at most TT + W - 1 consecutive planes: the CTA accumulates in a
+// shared-memory ring of that many planes (plane t at ring slot t mod (TT + W
+// - 1)), and before it adds a bin it writes out the planes that bin can no
+// longer reach -- each occupied tile of the stack exactly once -- and clears
+// their slots.  A visibility is one entry in each tile column its W x W taps
+// in (u, v) touch (at most 2 x 2), whatever the planes its W taps in w span.
 //
-// The tile's entries are split evenly over the CTA's warps; a warp takes its
+// A bin's entries are split evenly over the CTA's warps; a warp takes its
 // share in chunks of up to kChunk entries, in three steps:
 //   1. lane j prepares entry j of the chunk: its record, the part of its
-//      W x W x W footprint that lies in the tile (first tap and tap count
-//      along u, v and w) and the tile offset of that part's first cell;
+//      W x W x W footprint that lies in the column and in the plane chunk
+//      (first tap and tap count along u, v and w) and that part's first cell;
 //   2. the warp evaluates the chunk's 3W weight polynomials C(r - u'),
 //      C(s - v'), C(t - w'), one (entry, slot) pair per lane and round;
 //   3. entry after entry, the lanes take the (row, plane) pairs of the part,
@@ -285,42 +302,33 @@ __global__ void scan_add_kernel(uint32_t *__restrict__ out, const uint32_t *__re
 // entry, and each tap costs one weight product and one reduction per
 // component.
 // ---------------------------------------------------------------------------
-constexpr int kGridThreads = 256;
-constexpr int kGridWarps = kGridThreads / 32;
-constexpr int kRowPad = TU + 1;                    // shared row stride (floats)
-// Shared plane stride of a tile of R rows: R 17 + 8, which is 8 (mod 32) for
-// R = 32, 64 and 24 (mod 32) for R = 16; either way (17 b + stride c) mod 32
-// differs for every b < 7 and c < 4, so the (row, plane) pairs of one pass
-// hit distinct banks.
-template <int R>
-__host__ __device__ constexpr int plane_stride() { return R * kRowPad + 8; }
-template <int R>
-__host__ __device__ constexpr int tile_floats() { return TT * plane_stride<R>(); }
-constexpr int kCoefStride = 20;                    // kMaxDeg + 1 coefficients per slot, padded for float4 loads
 static_assert(kMaxDeg + 1 <= kCoefStride && kCoefStride % 4 == 0 && kMaxDeg == 16,
               "the Horner steps below read coefficients 0..16 as five float4");
-static_assert(tile_floats<16>() % 4 == 0 && tile_floats<32>() % 4 == 0 && tile_floats<64>() % 4 == 0,
-              "the tile is cleared in float4 stores");
+static_assert(plane_stride(16) % 4 == 0 && plane_stride(32) % 4 == 0 && plane_stride(64) % 4 == 0,
+              "ring planes are cleared in 16-byte stores");
 static_assert(kMaxW <= 15, "tap counts and first taps are packed in 4 bits");
+static_assert(ring_planes(kMaxW) <= 31, "ring slots are packed in 5 bits");
 constexpr int kGeneral = -1;                       // item shape: the part wraps an axis of a small grid
-constexpr int kChunk = 16;                         // entries a warp stages at a time
 
-// Dynamic shared memory of grid3d<W, R, DET>: the tile (re, im; FP32 sums, or
-// 64-bit fixed-point sums for the deterministic mode), the weight table, and
-// per warp the staged chunk (weights, items, values, offsets nu).
+// Dynamic shared memory of grid3d<W, R, DET> (grid_smem_bytes): the ring (re,
+// im; FP32 sums, or 64-bit fixed-point sums for the deterministic mode), the
+// weight table, and per warp the staged chunk (weights, items, values, nu).
 template <int W, int R, bool DET>
 struct GridSmem {
     static constexpr int S = 3 * W;                // weight slots per entry: u taps, v taps, w taps
     static constexpr int SP = S | 1;               // entry stride of the staged weights
-    static constexpr int ES = DET ? 8 : 4;         // bytes per tile cell component
+    static constexpr int ES = DET ? 8 : 4;         // bytes per cell component
+    static constexpr int RP = ring_planes(W);      // ring planes
+    static constexpr int PS = plane_stride(R);     // cells per ring plane (padded)
     static constexpr size_t re = 0;
-    static constexpr size_t im = re + (size_t)tile_floats<R>() * ES;
-    static constexpr size_t coef = im + (size_t)tile_floats<R>() * ES;
+    static constexpr size_t im = re + (size_t)RP * PS * ES;
+    static constexpr size_t coef = im + (size_t)RP * PS * ES;
     static constexpr size_t wt = coef + (size_t)S * kCoefStride * 4;
     static constexpr size_t item = wt + (size_t)kGridWarps * kChunk * SP * 4;
     static constexpr size_t val = item + (size_t)kGridWarps * kChunk * 16;
     static constexpr size_t nu = val + (size_t)kGridWarps * kChunk * 8;
     static constexpr size_t bytes = nu + (size_t)kGridWarps * kChunk * 16;
+    static_assert(bytes == grid_smem_bytes(W, R, DET), "the host's size of the gridding shared memory");
     static_assert(coef % 16 == 0 && wt % 16 == 0 && item % 16 == 0 && nu % 16 == 0, "float4 / int4 alignment");
 };
 
@@ -349,9 +357,6 @@ template <int OFF>
 __device__ __forceinline__ void red_shared_at(unsigned addr, float v) {
     asm volatile("red.shared.add.f32 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "f"(v) : "memory");
 }
-__device__ __forceinline__ void red_shared(unsigned addr, float v) {
-    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
 
 // The deterministic mode's shared-memory add: a contribution v becomes the
 // 64-bit integer nearest v 2^scale, and integer sums do not depend on the
@@ -362,7 +367,7 @@ __device__ __forceinline__ void red_shared_fixed_at(unsigned addr, float v, int 
     asm volatile("red.shared.add.u64 [%0+%1], %2;" ::"r"(addr), "n"(OFF), "l"(q) : "memory");
 }
 
-// One contribution to a tile cell component at byte address addr + OFF.
+// One contribution to a ring cell component at byte address addr + OFF.
 template <bool DET, int OFF>
 __device__ __forceinline__ void add_cell(unsigned addr, float v, int scale) {
     if constexpr (DET)
@@ -371,7 +376,7 @@ __device__ __forceinline__ void add_cell(unsigned addr, float v, int scale) {
         red_shared_at<OFF>(addr, v);
 }
 
-// Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a tile row (re and im at byte addresses).
+// Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a ring row (re and im at byte addresses).
 template <int W, bool DET, int A = 0>
 __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[W], int na, float pr, float pi,
                                         int scale) {
@@ -385,46 +390,108 @@ __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&
     }
 }
 
-// DET: the deterministic mode (WS_FLAG_DETERMINISTIC).  The tile sums in 64-bit
-// fixed point with a per-tile scale 2^scale chosen so that no sum can exceed
-// 2^62: |sum| <= E max|V~| wbound for the tile's E entries, wbound bounding
-// |C_x C_y C_z|.  The scale depends only on the tile's set of entries, and
-// integer additions do not depend on their order, so the tile -- and the dirty
-// image -- come out bit for bit the same whatever order the binning's atomics
-// and the warps' schedule give the entries.
+// Index j of 0 .. n-1 taken in the order 0, n-1, 1, n-2, ...: the tile
+// columns near the uv origin (both ends of the wrapped axes), which hold the
+// most entries, start first and do not trail the launch.
+__device__ __forceinline__ int centre_first(int j, int n) { return (j & 1) ? n - 1 - (j >> 1) : (j >> 1); }
+
+// Writes out the ring's slices (t-tiles) s in [from, to) and clears their
+// planes, when the ring holds planes [from TT, from TT + RP): a slice that the
+// chunk owns and a footprint touched (tile_occ) goes to the stack, its planes
+// past the ring's end as zeros (no footprint reached them).
 template <int W, int R, bool DET>
-__global__ void __launch_bounds__(kGridThreads, DET ? 2 : (R <= 32 ? 4 : 2))
+__device__ __forceinline__ void flush_slices(int from, int to, const Launch &L, int tv, int tu, int chunk_tt0,
+                                             int chunk_ntt, const uint8_t *__restrict__ tile_occ, int scale,
+                                             unsigned char *smem, float2 *__restrict__ stack, bool clear) {
+    using Sm = GridSmem<W, R, DET>;
+    constexpr int RP = Sm::RP, PS = Sm::PS;
+    const int ring_end = from * TT + RP;
+    const int last = min(to, from + (RP + TT - 1) / TT);
+    const size_t plane = (size_t)L.Np * L.Np;
+    for (int sl = max(from, chunk_tt0); sl < min(last, chunk_tt0 + chunk_ntt); ++sl) {
+        if (!tile_occ[((size_t)sl * L.ntv + tv) * L.ntu + tu]) continue;
+        // pairs of cells, ordered (plane, column block, row, pair) so that each
+        // column block's R rows go out as one contiguous run
+        for (int i = threadIdx.x; i < TT * R * TU / 2; i += kGridThreads) {
+            const int pair = i & 1, lr = (i >> 1) % R, blk = (i / (2 * R)) % (TU / CB), pl = i / (TU * R / 2);
+            const int lc = blk * CB + 2 * pair;
+            const int t = sl * TT + pl;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < ring_end) {
+                const int cell = (t % RP) * PS + lr * kRowPad + lc;
+                if constexpr (DET) {
+                    const long long *qre = reinterpret_cast<const long long *>(smem + Sm::re);
+                    const long long *qim = reinterpret_cast<const long long *>(smem + Sm::im);
+                    v = make_float4(ldexpf(__ll2float_rn(qre[cell]), -scale), ldexpf(__ll2float_rn(qim[cell]), -scale),
+                                    ldexpf(__ll2float_rn(qre[cell + 1]), -scale),
+                                    ldexpf(__ll2float_rn(qim[cell + 1]), -scale));
+                } else {
+                    const float *sre = reinterpret_cast<const float *>(smem + Sm::re);
+                    const float *sim = reinterpret_cast<const float *>(smem + Sm::im);
+                    v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
+                }
+            }
+            float2 *dst = stack + (size_t)(t - chunk_tt0 * TT) * plane + tiled_index(tv * R + lr, tu * TU + lc, L.Np);
+            *reinterpret_cast<float4 *>(dst) = v;
+        }
+    }
+    if (!clear) return;
+    __syncthreads();                                  // every cell is read before any is cleared
+    // planes [from TT, min(to TT, ring_end)), consecutive ring slots mod RP
+    constexpr int V4 = PS * Sm::ES / 16;              // 16-byte words per ring plane and component
+    const int t0 = from * TT, np = min(to * TT, ring_end) - t0;
+    float4 *qre = reinterpret_cast<float4 *>(smem + Sm::re), *qim = reinterpret_cast<float4 *>(smem + Sm::im);
+    for (int i = threadIdx.x; i < np * V4; i += kGridThreads) {
+        const int j = i / V4, w = i - j * V4;
+        const int slot = (t0 + j) % RP;
+        qre[slot * V4 + w] = make_float4(0.f, 0.f, 0.f, 0.f);
+        qim[slot * V4 + w] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// DET: the deterministic mode (WS_FLAG_DETERMINISTIC).  The ring sums in 64-bit
+// fixed point with one scale 2^scale for the CTA, chosen so that no sum can
+// exceed 2^62: |sum| <= E max|V~| wbound for the column's E entries, wbound
+// bounding |C_x C_y C_z|.  The scale depends only on the column's set of
+// entries, and integer additions do not depend on their order, so the stack
+// -- and the dirty image -- come out bit for bit the same whatever order the
+// binning's atomics and the warps' schedule give the entries.
+template <int W, int R, bool DET>
+__global__ void __launch_bounds__(kGridThreads, grid_ctas_per_sm(W, R, DET))
 grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
               const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ list,
-              uint32_t tile_base, int chunk_tt0, float wbound, float2 *__restrict__ stack) {
+              const uint8_t *__restrict__ tile_occ, int chunk_tt0, int chunk_ntt, float wbound,
+              float2 *__restrict__ stack) {
     using Sm = GridSmem<W, R, DET>;
-    constexpr int kPlaneStride = plane_stride<R>(), kTileFloats = tile_floats<R>(), ES = Sm::ES;
-    constexpr int S = Sm::S, SP = Sm::SP;
+    constexpr int PS = Sm::PS, RP = Sm::RP, ES = Sm::ES, S = Sm::S, SP = Sm::SP;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned tile_max;                     // DET: max |V~| of the tile's entries (float bits)
-    const uint32_t tile = tile_base + blockIdx.x;
-    const uint32_t beg = offsets[tile], end = offsets[tile + 1];
-    if (beg == end) return;                           // empty tile: the transforms treat it as zero
-    float *sre = reinterpret_cast<float *>(smem + Sm::re);
-    float *sim = reinterpret_cast<float *>(smem + Sm::im);
+    __shared__ unsigned col_max;                      // DET: max |V~| of the column's entries (float bits)
+    const int tu = centre_first(blockIdx.x % L.ntu, L.ntu);
+    const int tv = centre_first(blockIdx.x / L.ntu, L.ntv);
+    // the bins whose footprints reach the chunk's planes [plo, phi)
+    const int k_lo = max(0, chunk_tt0 - (TT + W - 2) / TT), k_hi = chunk_tt0 + chunk_ntt;
+    const int plo = chunk_tt0 * TT, phi = plo + chunk_ntt * TT;
+    const uint32_t *__restrict__ off = offsets + ((size_t)tv * L.ntu + tu) * L.ntt;
+    const uint32_t all_beg = off[k_lo], all_end = off[k_hi];
+    if (all_beg == all_end) return;                  // untouched column: the transforms treat it as zero
     float *scoef = reinterpret_cast<float *>(smem + Sm::coef);
-    const int tu = tile % L.ntu;
-    const int tv = (tile / L.ntu) % L.ntv;
-    const int tt = tile / (L.ntu * L.ntv);
-    for (int i = threadIdx.x; i < kTileFloats * ES / 16; i += kGridThreads) {
-        reinterpret_cast<float4 *>(sre)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        reinterpret_cast<float4 *>(sim)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        float4 *qre = reinterpret_cast<float4 *>(smem + Sm::re), *qim = reinterpret_cast<float4 *>(smem + Sm::im);
+        for (int i = threadIdx.x; i < RP * PS * ES / 16; i += kGridThreads) {
+            qre[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            qim[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     if constexpr (DET) {
-        if (threadIdx.x == 0) tile_max = 0u;
+        if (threadIdx.x == 0) col_max = 0u;
         __syncthreads();
         float m = 0.f;
-        for (uint32_t e = beg + threadIdx.x; e < end; e += kGridThreads) {
+        for (uint32_t e = all_beg + threadIdx.x; e < all_end; e += kGridThreads) {
             const VisRec r = rec[list[e]];
             m = fmaxf(m, fmaxf(fabsf(r.vre), fabsf(r.vim)));
         }
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(&tile_max, __float_as_uint(m));   // non-negative floats order as integers
+        if ((threadIdx.x & 31) == 0) atomicMax(&col_max, __float_as_uint(m));   // non-negative floats order as integers
     }
     // slot l < 3W is (axis l / W, tap l % W); coef holds the (u, v) table and
     // then the w table, W x (deg + 1) each; coefficients past deg are zero
@@ -436,138 +503,135 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     __syncthreads();
     const int Np = L.Np;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u_org = tu * TU, v_org = tv * R, t_org = tt * TT;
+    const int u_org = tu * TU, v_org = tv * R;
     float *wts = reinterpret_cast<float *>(smem + Sm::wt) + warp * kChunk * SP;
     int4 *items = reinterpret_cast<int4 *>(smem + Sm::item) + warp * kChunk;
     float2 *vals = reinterpret_cast<float2 *>(smem + Sm::val) + warp * kChunk;
     float4 *nus = reinterpret_cast<float4 *>(smem + Sm::nu) + warp * kChunk;
-    const unsigned re_base = (unsigned)__cvta_generic_to_shared(sre);
-    const unsigned im_base = (unsigned)__cvta_generic_to_shared(sim);
-    const uint32_t E = end - beg;
+    const unsigned re_base = (unsigned)__cvta_generic_to_shared(smem + Sm::re);
+    const unsigned im_base = (unsigned)__cvta_generic_to_shared(smem + Sm::im);
     int scale = 0;                                   // DET: sums are kept as integers in units of 2^-scale
     if constexpr (DET) {
-        const float bound = (float)E * __uint_as_float(tile_max) * wbound;
+        const float bound = (float)(all_end - all_beg) * __uint_as_float(col_max) * wbound;
         if (bound > 0.f) {
             int ex;
             frexpf(bound, &ex);                          // bound < 2^ex
             scale = 62 - ex;
         }
     }
-    // this warp's share of the tile's entries
-    const uint32_t per = (E + kGridWarps - 1) / kGridWarps;
-    const uint32_t wbeg = beg + min(E, warp * per), wend = beg + min(E, (warp + 1) * per);
-    for (uint32_t cbeg = wbeg; cbeg < wend; cbeg += kChunk) {
-        const int n = (int)min((uint32_t)kChunk, wend - cbeg);
-        // 1. lane j: entry j's part of the footprint inside the tile
-        if (lane < n) {
-            const uint32_t k = list[cbeg + lane];
-            const VisRec r = rec[k];
-            Span su[2], sv[2];
-            const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
-            const int nsv = tile_spans(v_org, r.s0, Np, W, R, sv[0], sv[1]);
-            const int dt = t_org - r.t0;
-            const int c0 = max(0, dt), c1 = min(W, dt + TT);
-            int4 it;
-            if (nsu == 1 && nsv == 1) {
-                const int na = su[0].a1 - su[0].a0, nb = sv[0].a1 - sv[0].a0, nc = c1 - c0;
-                it.x = (c0 - dt) * kPlaneStride + (sv[0].a0 - sv[0].off) * kRowPad + (su[0].a0 - su[0].off);
-                it.y = na | nb << 4 | max(nc, 0) << 8 | su[0].a0 << 12 | sv[0].a0 << 16 | c0 << 20;
-                it.z = __float_as_int(1.0f / (float)nb);
-            } else {
-                it.x = 0;
-                it.y = kGeneral;
-                it.z = 0;
-            }
-            it.w = (int)k;
-            items[lane] = it;
-            vals[lane] = make_float2(r.vre, r.vim);
-            nus[lane] = make_float4(r.nux, r.nuy, r.nuz, 0.f);
+    int cur = -1;                                    // t-tile of the ring's first plane; -1: none yet
+    for (int k = k_lo; k < k_hi; ++k) {
+        const uint32_t beg = off[k], end = off[k + 1];
+        if (beg == end) continue;
+        if (cur >= 0) {
+            // bin k reaches planes [k TT, k TT + RP): the ring's planes before k TT are final
+            __syncthreads();
+            flush_slices<W, R, DET>(cur, k, L, tv, tu, chunk_tt0, chunk_ntt, tile_occ, scale, smem, stack, true);
+            __syncthreads();
         }
-        __syncwarp();
-        // 2. the chunk's weights: pair q = (entry j, slot l), Horner from nu^16 down
-        for (int q = lane; q < n * S; q += 32) {
-            const int j = q / S, l = q - j * S, axis = l / W;
-            const float4 nv = nus[j];
-            const float nu = axis == 0 ? nv.x : (axis == 1 ? nv.y : nv.z);
-            const float4 *c = reinterpret_cast<const float4 *>(scoef + l * kCoefStride);
-            float acc = c[4].x;
-#pragma unroll
-            for (int b = 3; b >= 0; --b) {
-                const float4 c4 = c[b];
-                acc = fmaf(acc, nu, c4.w);
-                acc = fmaf(acc, nu, c4.z);
-                acc = fmaf(acc, nu, c4.y);
-                acc = fmaf(acc, nu, c4.x);
-            }
-            wts[j * SP + l] = acc;
-        }
-        __syncwarp();
-        // 3. add the chunk's entries one after the other
-        for (int j = 0; j < n; ++j) {
-            const int4 it = items[j];
-            const float2 V = vals[j];
-            const float *wt = wts + j * SP;
-            if (it.y != kGeneral) {
-                const int na = it.y & 15, nb = (it.y >> 4) & 15, nc = (it.y >> 8) & 15;
-                const int a0 = (it.y >> 12) & 15, b0 = (it.y >> 16) & 15, cw0 = (it.y >> 20) & 15;
-                const float inv_nb = __int_as_float(it.z);
-                const int nbc = nb * nc;
-                // the part's u-tap weights, all read before the first reduction
-                float wx[W];
-#pragma unroll
-                for (int a = 0; a < W; ++a) wx[a] = a < na ? wt[a0 + a] : 0.f;
-                for (int q = lane; q < nbc; q += 32) {
-                    // q = cc nb + bb, q < 144: (q + 1/2) / nb is at least 1/24 from an integer
-                    const int cc = __float2int_rz(((float)q + 0.5f) * inv_nb), bb = q - cc * nb;
-                    const float wyz = wt[W + b0 + bb] * wt[2 * W + cw0 + cc];
-                    const unsigned off = (unsigned)(it.x + cc * kPlaneStride + bb * kRowPad) * ES;
-                    add_row<W, DET>(re_base + off, im_base + off, wx, na, V.x * wyz, V.y * wyz, scale);
-                }
-            } else {
-                // the part wraps around an axis (N' < W + R): every span pair, taps one by one
-                const VisRec r = rec[it.w];
+        cur = k;
+        // this warp's share of the bin's entries
+        const uint32_t E = end - beg;
+        const uint32_t per = (E + kGridWarps - 1) / kGridWarps;
+        const uint32_t wbeg = beg + min(E, warp * per), wend = beg + min(E, (warp + 1) * per);
+        for (uint32_t cbeg = wbeg; cbeg < wend; cbeg += kChunk) {
+            const int n = (int)min((uint32_t)kChunk, wend - cbeg);
+            // 1. lane j: entry j's part of the footprint inside the column and the chunk's planes
+            if (lane < n) {
+                const uint32_t kv = list[cbeg + lane];
+                const VisRec r = rec[kv];
                 Span su[2], sv[2];
                 const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
                 const int nsv = tile_spans(v_org, r.s0, Np, W, R, sv[0], sv[1]);
-                const int dt = t_org - r.t0;
-                const int c0 = max(0, dt), c1 = min(W, dt + TT);
-                for (int iu = 0; iu < nsu; ++iu)
-                    for (int iv = 0; iv < nsv; ++iv) {
-                        const int na = su[iu].a1 - su[iu].a0, nb = sv[iv].a1 - sv[iv].a0, nc = c1 - c0;
-                        for (int q = lane; q < na * nb * nc; q += 32) {
-                            const int a = su[iu].a0 + q % na, b = sv[iv].a0 + (q / na) % nb, c = c0 + q / (na * nb);
-                            const float w = wt[a] * wt[W + b] * wt[2 * W + c];
-                            const unsigned off =
-                                (unsigned)((c - dt) * kPlaneStride + (b - sv[iv].off) * kRowPad + (a - su[iu].off)) * ES;
-                            add_cell<DET, 0>(re_base + off, V.x * w, scale);
-                            add_cell<DET, 0>(im_base + off, V.y * w, scale);
-                        }
-                    }
+                const int c0 = max(0, plo - r.t0), c1 = min(W, phi - r.t0);
+                int4 it;
+                if (nsu == 1 && nsv == 1) {
+                    const int na = su[0].a1 - su[0].a0, nb = sv[0].a1 - sv[0].a0, nc = max(c1 - c0, 0);
+                    const int slot = (r.t0 + c0) % RP;      // ring slot of the part's first plane
+                    it.x = (sv[0].a0 - sv[0].off) * kRowPad + (su[0].a0 - su[0].off);
+                    it.y = na | nb << 4 | nc << 8 | su[0].a0 << 12 | sv[0].a0 << 16 | c0 << 20 | slot << 24;
+                    it.z = __float_as_int(1.0f / (float)nb);
+                } else {
+                    it.x = 0;
+                    it.y = kGeneral;
+                    it.z = 0;
+                }
+                it.w = (int)kv;
+                items[lane] = it;
+                vals[lane] = make_float2(r.vre, r.vim);
+                nus[lane] = make_float4(r.nux, r.nuy, r.nuz, 0.f);
             }
+            __syncwarp();
+            // 2. the chunk's weights: pair q = (entry j, slot l), Horner from nu^16 down
+            for (int q = lane; q < n * S; q += 32) {
+                const int j = q / S, l = q - j * S, axis = l / W;
+                const float4 nv = nus[j];
+                const float nu = axis == 0 ? nv.x : (axis == 1 ? nv.y : nv.z);
+                const float4 *c = reinterpret_cast<const float4 *>(scoef + l * kCoefStride);
+                float acc = c[4].x;
+#pragma unroll
+                for (int b = 3; b >= 0; --b) {
+                    const float4 c4 = c[b];
+                    acc = fmaf(acc, nu, c4.w);
+                    acc = fmaf(acc, nu, c4.z);
+                    acc = fmaf(acc, nu, c4.y);
+                    acc = fmaf(acc, nu, c4.x);
+                }
+                wts[j * SP + l] = acc;
+            }
+            __syncwarp();
+            // 3. add the chunk's entries one after the other
+            for (int j = 0; j < n; ++j) {
+                const int4 it = items[j];
+                const float2 V = vals[j];
+                const float *wt = wts + j * SP;
+                if (it.y != kGeneral) {
+                    const int na = it.y & 15, nb = (it.y >> 4) & 15, nc = (it.y >> 8) & 15;
+                    const int a0 = (it.y >> 12) & 15, b0 = (it.y >> 16) & 15, cw0 = (it.y >> 20) & 15;
+                    const int slot0 = (it.y >> 24) & 31;
+                    const float inv_nb = __int_as_float(it.z);
+                    const int nbc = nb * nc;
+                    // the part's u-tap weights, all read before the first reduction
+                    float wx[W];
+#pragma unroll
+                    for (int a = 0; a < W; ++a) wx[a] = a < na ? wt[a0 + a] : 0.f;
+                    for (int q = lane; q < nbc; q += 32) {
+                        // q = cc nb + bb, q < 144: (q + 1/2) / nb is at least 1/24 from an integer
+                        const int cc = __float2int_rz(((float)q + 0.5f) * inv_nb), bb = q - cc * nb;
+                        const float wyz = wt[W + b0 + bb] * wt[2 * W + cw0 + cc];
+                        int slot = slot0 + cc;
+                        if (slot >= RP) slot -= RP;
+                        const unsigned o = (unsigned)(it.x + slot * PS + bb * kRowPad) * ES;
+                        add_row<W, DET>(re_base + o, im_base + o, wx, na, V.x * wyz, V.y * wyz, scale);
+                    }
+                } else {
+                    // the part wraps around an axis (N' < W + R): every span pair, taps one by one
+                    const VisRec r = rec[it.w];
+                    Span su[2], sv[2];
+                    const int nsu = tile_spans(u_org, r.r0, Np, W, TU, su[0], su[1]);
+                    const int nsv = tile_spans(v_org, r.s0, Np, W, R, sv[0], sv[1]);
+                    const int c0 = max(0, plo - r.t0), c1 = min(W, phi - r.t0);
+                    for (int iu = 0; iu < nsu; ++iu)
+                        for (int iv = 0; iv < nsv; ++iv) {
+                            const int na = su[iu].a1 - su[iu].a0, nb = sv[iv].a1 - sv[iv].a0, nc = c1 - c0;
+                            for (int q = lane; q < na * nb * nc; q += 32) {
+                                const int a = su[iu].a0 + q % na, b = sv[iv].a0 + (q / na) % nb, c = c0 + q / (na * nb);
+                                const float w = wt[a] * wt[W + b] * wt[2 * W + c];
+                                const unsigned o = (unsigned)(((r.t0 + c) % RP) * PS + (b - sv[iv].off) * kRowPad +
+                                                              (a - su[iu].off)) *
+                                                   ES;
+                                add_cell<DET, 0>(re_base + o, V.x * w, scale);
+                                add_cell<DET, 0>(im_base + o, V.y * w, scale);
+                            }
+                        }
+                }
+            }
+            __syncwarp();                              // the chunk's staging is read before the next overwrites it
         }
-        __syncwarp();                                  // the chunk's staging is read before the next overwrites it
     }
     __syncthreads();
-    const size_t plane = (size_t)Np * Np;
-    const int p0 = t_org - chunk_tt0 * TT;
-    // pairs of cells, ordered (plane, column block, row, pair) so that each
-    // column block's R rows go out as one contiguous run
-    for (int i = threadIdx.x; i < TT * R * TU / 2; i += kGridThreads) {
-        const int pair = i & 1, lr = (i >> 1) % R, blk = (i / (2 * R)) % (TU / CB), pl = i / (TU * R / 2);
-        const int lc = blk * CB + 2 * pair;
-        const int cell = pl * kPlaneStride + lr * kRowPad + lc;
-        float4 v;
-        if constexpr (DET) {
-            const long long *qre = reinterpret_cast<const long long *>(sre);
-            const long long *qim = reinterpret_cast<const long long *>(sim);
-            v = make_float4(ldexpf(__ll2float_rn(qre[cell]), -scale), ldexpf(__ll2float_rn(qim[cell]), -scale),
-                            ldexpf(__ll2float_rn(qre[cell + 1]), -scale), ldexpf(__ll2float_rn(qim[cell + 1]), -scale));
-        } else {
-            v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
-        }
-        float2 *dst = stack + (size_t)(p0 + pl) * plane + tiled_index(v_org + lr, u_org + lc, Np);
-        *reinterpret_cast<float4 *>(dst) = v;
-    }
+    flush_slices<W, R, DET>(cur, cur + (RP + TT - 1) / TT, L, tv, tu, chunk_tt0, chunk_ntt, tile_occ, scale, smem,
+                            stack, false);
 }
 
 // Algorithm 6 step 2: image x h_x h_y h_z.
@@ -701,46 +765,27 @@ cudaError_t launch_bound_grid_records(const ws_plan_s *p, const double *uvw, con
 cudaError_t launch_bin(ws_plan_s *p, int64_t M, bool grid, cudaStream_t s) {
     const int64_t n = p->ntiles + 1;
     cudaError_t e = cudaMemsetAsync(p->d_counts, 0, n * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_tile_occ, 0, (size_t)p->ntiles, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
     if (e != cudaSuccess) return e;
     if (M > 0 && grid)
-        count_kernel<true><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts);
+        count_kernel<true><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts, p->d_tile_occ);
     else if (M > 0)
-        count_kernel<false><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts);
+        count_kernel<false><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts, p->d_tile_occ);
     const int nb = (int)((n + kScanPerBlock - 1) / kScanPerBlock);
     scan_block_kernel<<<nb, kScanThreads, 0, s>>>(p->d_counts, p->d_offsets, p->d_blocksums, n);
     scan_sums_kernel<<<1, kScanThreads, 0, s>>>(p->d_blocksums, nb);
     scan_add_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p->d_offsets, p->d_blocksums, n);
+    if (M == 0) return cudaGetLastError();
     e = cudaMemsetAsync(p->d_counts, 0, n * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    if (M == 0) return cudaGetLastError();
     if (grid)
         scatter_kernel<true><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_offsets, p->d_counts,
                                                                p->d_list);
     else
         scatter_kernel<false><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_offsets,
                                                                 p->d_counts, p->d_list);
-    return cudaGetLastError();
-}
-
-// Degridding's occupancy: count the footprints' (visibility, tile) pairs in
-// the counters the binning has finished with, then mark the tiles.
-cudaError_t launch_mark(const ws_plan_s *p, int64_t M, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
-    if (e != cudaSuccess) return e;
-    if (M == 0) return cudaMemsetAsync(p->d_tile_occ, 0, (size_t)p->ntiles, s);
-    e = cudaMemsetAsync(p->d_counts, 0, (size_t)p->ntiles * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    count_kernel<true><<<blocks_for(M, 256), 256, 0, s>>>(p->L, p->d_rec, M, p->d_counts);
-    occ_kernel<true><<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_counts, p->ntiles, p->d_tile_occ,
-                                                                p->d_col_occ);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mark_grid(const ws_plan_s *p, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_col_occ, 0, (size_t)p->L.ntt * p->L.ntu, s);
-    if (e != cudaSuccess) return e;
-    occ_kernel<false><<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_offsets, p->ntiles, p->d_tile_occ,
-                                                                 p->d_col_occ);
+    strip_occ_kernel<<<blocks_for(p->ntiles, 256), 256, 0, s>>>(p->L, p->d_tile_occ, p->ntiles, p->d_col_occ);
     return cudaGetLastError();
 }
 
@@ -752,18 +797,17 @@ cudaError_t launch_occ_count(const ws_plan_s *p, cudaStream_t s) {
 }
 
 cudaError_t launch_grid_chunk(const ws_plan_s *p, int chunk, int planes, cudaStream_t s) {
-    const int tiles_per_tt = p->L.ntu * p->L.ntv;
-    const int chunk_tt0 = chunk * (p->P / TT);
-    const uint32_t tile_base = (uint32_t)chunk_tt0 * tiles_per_tt;
-    const unsigned nblocks = (unsigned)(planes / TT) * tiles_per_tt;
-    if (nblocks == 0) return cudaSuccess;
+    const int chunk_tt0 = chunk * (p->P / TT), chunk_ntt = planes / TT;
+    const unsigned nblocks = (unsigned)p->L.ntu * p->L.ntv;      // one CTA per tile column
+    if (chunk_ntt == 0) return cudaSuccess;
     const int R = p->L.tv;
     const bool det = (p->flags & WS_FLAG_DETERMINISTIC) != 0;
     auto go = [&](auto kernel, size_t smem) -> cudaError_t {
+        if (smem > kMaxGridSmem) return cudaErrorInvalidValue;   // set_tile_rows keeps this from happening
         const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         kernel<<<nblocks, kGridThreads, smem, s>>>(p->L, p->d_wcoef, p->wdeg, p->d_rec, p->d_offsets, p->d_list,
-                                                   tile_base, chunk_tt0, p->wbound, p->d_stack);
+                                                   p->d_tile_occ, chunk_tt0, chunk_ntt, p->wbound, p->d_stack);
         return cudaGetLastError();
     };
 #define WS_GRID_CASE(w)                                                                                       \

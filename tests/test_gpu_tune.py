@@ -32,7 +32,7 @@ def test_tuner_cache_and_every_tile_shape(dev, tmp_path, monkeypatch):
     uvw, vis, img = _tensors(c, dev)
     cache = tmp_path / "tune.json"
     with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], device=dev) as p:
-        assert p.tile_rows == 32
+        assert p.tile_rows == 16
         rows = p.tune(uvw, vis, img, cache_path=str(cache))
         assert rows in (16, 32, 64) and p.tile_rows == rows
         data = json.loads(cache.read_text())
@@ -80,5 +80,5 @@ def test_tile_rows_must_divide_the_grid(dev, tmp_path, monkeypatch):
     cache.write_text(json.dumps(data))
     monkeypatch.setenv("WS_TUNE_CACHE", str(cache))
     with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], device=dev) as p:
-        assert p.tile_rows == 32                       # the invalid entry is ignored
+        assert p.tile_rows == 16                       # the invalid entry is ignored
         assert _lib.WS_OK == 0
