@@ -36,9 +36,11 @@ constexpr int kMaxDeg = 16;
 
 // Gridding kernel shape: 256 threads; each warp stages kChunk entries at a
 // time.  Shared memory holds a ring of TT + W - 1 w-planes of the tile column
-// (rows padded to TU + 1 floats, planes to tv (TU + 1) + 8 floats; re and im,
-// FP32 or, deterministic, 64-bit fixed point), the weight table (3W slots of
-// kCoefStride coefficients) and the warps' staged chunks.
+// (re and im, FP32 or, deterministic, 64-bit fixed point; rows padded to TU +
+// 1 cells, planes to plane_stride cells), the weight table (3W slots of
+// kCoefStride coefficients) and the warps' staged chunks (per entry its u
+// weights from the first tap inside the tile, padded to a multiple of 4, then
+// its v and w weights).
 constexpr int kGridThreads = 256;
 constexpr int kGridWarps = kGridThreads / 32;
 constexpr int kChunk = 16;
@@ -47,11 +49,21 @@ constexpr int kCoefStride = 20;
 constexpr size_t kMaxGridSmem = 227 * 1024;     // dynamic shared memory of one CTA
 constexpr size_t kSmemPerSM = 228 * 1024;
 WS_HD constexpr int ring_planes(int W) { return TT + W - 1; }
-WS_HD constexpr int plane_stride(int rows) { return rows * kRowPad + 8; }
+// Cells per ring plane: rows x 17 padded to 20 (mod 32).  The add loop's lanes
+// take (row, plane) pairs of a footprint; with the row stride 17, the plane
+// strides that are multiples of 4 (16-byte clears) collide least for 20 (mod
+// 32): 1.52 lanes per bank on average over the footprint shapes of W = 7,
+// against 1.73 for 8 or 24 (mod 32).
+WS_HD constexpr int plane_stride(int rows) { return rows * kRowPad + ((20 - rows * kRowPad) % 32 + 32) % 32; }
+WS_HD constexpr size_t ring_bytes(int W, int rows, bool det) {
+    return ((size_t)ring_planes(W) * plane_stride(rows) * (det ? 8 : 4) + 15) / 16 * 16;   // one component
+}
+WS_HD constexpr int wx_span(int W) { return (W + 3) / 4 * 4; }                // staged u weights
+WS_HD constexpr int stage_stride(int W) { return (wx_span(W) + 2 * W + 3) / 4 * 4; }   // floats per entry
 WS_HD constexpr size_t grid_smem_bytes(int W, int rows, bool det) {
-    return (size_t)2 * ring_planes(W) * plane_stride(rows) * (det ? 8 : 4)      // ring, re and im
+    return 2 * ring_bytes(W, rows, det)                                           // ring, re and im
            + (size_t)3 * W * kCoefStride * 4                                      // weight table
-           + (size_t)kGridWarps * kChunk * ((3 * W) | 1) * 4                      // staged weights
+           + (size_t)kGridWarps * kChunk * stage_stride(W) * 4                    // staged weights
            + (size_t)kGridWarps * kChunk * (16 + 8 + 16);                         // items, values, nu
 }
 // CTAs of the gridding kernel that fit on one SM (1 KB reserved per CTA), at most 4

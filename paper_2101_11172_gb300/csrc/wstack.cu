@@ -316,13 +316,14 @@ constexpr int kGeneral = -1;                       // item shape: the part wraps
 template <int W, int R, bool DET>
 struct GridSmem {
     static constexpr int S = 3 * W;                // weight slots per entry: u taps, v taps, w taps
-    static constexpr int SP = S | 1;               // entry stride of the staged weights
+    static constexpr int WX = wx_span(W);          // staged u weights, from the part's first tap
+    static constexpr int SP = stage_stride(W);     // entry stride of the staged weights: u, v, w
     static constexpr int ES = DET ? 8 : 4;         // bytes per cell component
     static constexpr int RP = ring_planes(W);      // ring planes
     static constexpr int PS = plane_stride(R);     // cells per ring plane (padded)
     static constexpr size_t re = 0;
-    static constexpr size_t im = re + (size_t)RP * PS * ES;
-    static constexpr size_t coef = im + (size_t)RP * PS * ES;
+    static constexpr size_t im = re + ring_bytes(W, R, DET);
+    static constexpr size_t coef = im + ring_bytes(W, R, DET);
     static constexpr size_t wt = coef + (size_t)S * kCoefStride * 4;
     static constexpr size_t item = wt + (size_t)kGridWarps * kChunk * SP * 4;
     static constexpr size_t val = item + (size_t)kGridWarps * kChunk * 16;
@@ -378,7 +379,7 @@ __device__ __forceinline__ void add_cell(unsigned addr, float v, int scale) {
 
 // Adds (pr, pi) x wx[a] to cells a = 0 .. na - 1 of a ring row (re and im at byte addresses).
 template <int W, bool DET, int A = 0>
-__device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[W], int na, float pr, float pi,
+__device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&wx)[wx_span(W)], int na, float pr, float pi,
                                         int scale) {
     if constexpr (A < W) {
         if (A < na) {
@@ -463,7 +464,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
               const uint8_t *__restrict__ tile_occ, int chunk_tt0, int chunk_ntt, float wbound,
               float2 *__restrict__ stack) {
     using Sm = GridSmem<W, R, DET>;
-    constexpr int PS = Sm::PS, RP = Sm::RP, ES = Sm::ES, S = Sm::S, SP = Sm::SP;
+    constexpr int PS = Sm::PS, RP = Sm::RP, ES = Sm::ES, S = Sm::S, SP = Sm::SP, WX = Sm::WX;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned col_max;                      // DET: max |V~| of the column's entries (float bits)
     const int tu = centre_first(blockIdx.x % L.ntu, L.ntu);
@@ -562,7 +563,8 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                 nus[lane] = make_float4(r.nux, r.nuy, r.nuz, 0.f);
             }
             __syncwarp();
-            // 2. the chunk's weights: pair q = (entry j, slot l), Horner from nu^16 down
+            // 2. the chunk's weights: pair q = (entry j, slot l), Horner from nu^16
+            //    down; the u weights are kept from the part's first tap a0 on
             for (int q = lane; q < n * S; q += 32) {
                 const int j = q / S, l = q - j * S, axis = l / W;
                 const float4 nv = nus[j];
@@ -577,7 +579,12 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                     acc = fmaf(acc, nu, c4.y);
                     acc = fmaf(acc, nu, c4.x);
                 }
-                wts[j * SP + l] = acc;
+                int pos = WX + l - W;
+                if (axis == 0) {
+                    const int y = items[j].y;
+                    pos = l - (y == kGeneral ? 0 : (y >> 12) & 15);
+                }
+                if (pos >= 0) wts[j * SP + pos] = acc;
             }
             __syncwarp();
             // 3. add the chunk's entries one after the other
@@ -587,18 +594,25 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                 const float *wt = wts + j * SP;
                 if (it.y != kGeneral) {
                     const int na = it.y & 15, nb = (it.y >> 4) & 15, nc = (it.y >> 8) & 15;
-                    const int a0 = (it.y >> 12) & 15, b0 = (it.y >> 16) & 15, cw0 = (it.y >> 20) & 15;
+                    const int b0 = (it.y >> 16) & 15, cw0 = (it.y >> 20) & 15;
                     const int slot0 = (it.y >> 24) & 31;
                     const float inv_nb = __int_as_float(it.z);
                     const int nbc = nb * nc;
-                    // the part's u-tap weights, all read before the first reduction
-                    float wx[W];
+                    // the part's u-tap weights (staged from its first tap on; those
+                    // past na are not used), all read before the first reduction
+                    float wx[WX];
 #pragma unroll
-                    for (int a = 0; a < W; ++a) wx[a] = a < na ? wt[a0 + a] : 0.f;
+                    for (int a4 = 0; a4 < WX / 4; ++a4) {
+                        const float4 v = reinterpret_cast<const float4 *>(wt)[a4];
+                        wx[4 * a4] = v.x;
+                        wx[4 * a4 + 1] = v.y;
+                        wx[4 * a4 + 2] = v.z;
+                        wx[4 * a4 + 3] = v.w;
+                    }
                     for (int q = lane; q < nbc; q += 32) {
                         // q = cc nb + bb, q < 144: (q + 1/2) / nb is at least 1/24 from an integer
                         const int cc = __float2int_rz(((float)q + 0.5f) * inv_nb), bb = q - cc * nb;
-                        const float wyz = wt[W + b0 + bb] * wt[2 * W + cw0 + cc];
+                        const float wyz = wt[WX + b0 + bb] * wt[WX + W + cw0 + cc];
                         int slot = slot0 + cc;
                         if (slot >= RP) slot -= RP;
                         const unsigned o = (unsigned)(it.x + slot * PS + bb * kRowPad) * ES;
@@ -616,7 +630,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
                             const int na = su[iu].a1 - su[iu].a0, nb = sv[iv].a1 - sv[iv].a0, nc = c1 - c0;
                             for (int q = lane; q < na * nb * nc; q += 32) {
                                 const int a = su[iu].a0 + q % na, b = sv[iv].a0 + (q / na) % nb, c = c0 + q / (na * nb);
-                                const float w = wt[a] * wt[W + b] * wt[2 * W + c];
+                                const float w = wt[a] * wt[WX + b] * wt[WX + W + c];
                                 const unsigned o = (unsigned)(((r.t0 + c) % RP) * PS + (b - sv[iv].off) * kRowPad +
                                                               (a - su[iu].off)) *
                                                    ES;
