@@ -52,3 +52,25 @@ def test_dirty_image_independent_of_visibility_order(dev, N):
     d1 = d1.astype(np.complex128)
     assert rel(d1, d_ref) < tol
     assert_elementwise(d1, d_ref, tol, f"deterministic grid, N = {N}")
+
+
+def test_deterministic_across_plane_chunks_and_wide_footprints(dev, monkeypatch):
+    # W = 10: a footprint reaches 3 t-tiles, so a plane chunk also takes the
+    # bins of the two t-tiles before it (only their planes inside the chunk)
+    from paper_2101_11172_gb300 import WS_FLAG_DETERMINISTIC, _lib
+    from paper_2101_11172_gb300.wstack import Plan
+    c = case(N=64, M=4000, W=10, wfac=40.0, seed=97)
+    perm = np.random.default_rng(7).permutation(c["M"])
+    monkeypatch.setenv("WS_PLANES_PER_CHUNK", "8")
+    with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], flags=WS_FLAG_DETERMINISTIC,
+              device=dev) as p:
+        assert p.planes_per_chunk == 8 and p.Nw > 24
+        d1 = _grid(p, c["uvw"], c["vis"], dev)
+        assert p.last_status == _lib.WS_OK
+        d3 = _grid(p, np.ascontiguousarray(c["uvw"][perm]), np.ascontiguousarray(c["vis"][perm]), dev)
+        assert np.array_equal(d1, d3)
+    g, lm, _, d_ref = oracle_pair(c)
+    tol = tol_for(c["W"], g.x0)
+    d1 = d1.astype(np.complex128)
+    assert rel(d1, d_ref) < tol, rel(d1, d_ref)
+    assert_elementwise(d1, d_ref, tol, "deterministic grid, W = 10, 8-plane chunks")
