@@ -82,3 +82,30 @@ def test_tile_rows_must_divide_the_grid(dev, tmp_path, monkeypatch):
     with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], device=dev) as p:
         assert p.tile_rows == 16                       # the invalid entry is ignored
         assert _lib.WS_OK == 0
+
+
+def test_tiles_spanning_the_whole_grid(dev, tmp_path, monkeypatch):
+    # N' = 32 with 32-row tiles: one tile holds every row of the grid, so the
+    # footprints near its edge wrap around inside the tile (the gridding
+    # kernel's two-span path, and a degridding bin that is a whole column)
+    from paper_2101_11172_gb300.wstack import Plan
+    c = case(N=16, M=1500, W=7, seed=29)
+    uvw, vis, img = _tensors(c, dev)
+    cache = tmp_path / "tune.json"
+    with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], device=dev) as p:
+        assert p.Np == 32
+        p.tune(uvw, vis, img, cache_path=str(cache))
+    data = json.loads(cache.read_text())
+    (key, entry), = data.items()
+    data[key]["tile_rows"] = 32
+    cache.write_text(json.dumps(data))
+    monkeypatch.setenv("WS_TUNE_CACHE", str(cache))
+    with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], device=dev) as p:
+        assert p.tile_rows == 32
+        v = p.degrid(img, uvw).cpu().numpy().astype(np.complex128)
+        d = p.grid(uvw, vis).cpu().numpy().astype(np.complex128)
+    g, lm, v_ref, d_ref = oracle_pair(c)
+    tol = tol_for(c["W"], g.x0)
+    assert rel(v, v_ref) < tol and rel(d, d_ref) < tol, (rel(v, v_ref), rel(d, d_ref))
+    assert_elementwise(v, v_ref, tol, "degrid, N' = 32, 32-row tiles")
+    assert_elementwise(d, d_ref, tol, "grid, N' = 32, 32-row tiles")
