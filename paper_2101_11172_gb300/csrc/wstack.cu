@@ -683,8 +683,12 @@ degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec 
                 const float2 *__restrict__ stack, int plane0, int planes, float2 *__restrict__ vis) {
     constexpr int kPasses = (W * W + 31) / 32;
     __shared__ float swt[kDegridThreads / 32][3 * W];
-    __shared__ float scoef[2 * W * (kMaxDeg + 1)];       // (u, v) table, then the w table
-    for (int i = threadIdx.x; i < 2 * W * (deg + 1); i += kDegridThreads) scoef[i] = coef[i];
+    // the (u, v) table, then the w table: 2W rows of kCoefStride coefficients, zero past deg
+    __shared__ __align__(16) float scoef[2 * W * kCoefStride];
+    for (int i = threadIdx.x; i < 2 * W * kCoefStride; i += kDegridThreads) {
+        const int row = i / kCoefStride, m = i - row * kCoefStride;
+        scoef[i] = m <= deg ? coef[row * (deg + 1) + m] : 0.f;
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t n = (int64_t)*n_order;                   // entries of the sorted list (dropped ones excluded)
@@ -705,24 +709,38 @@ degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec 
         for (int l = lane; l < 3 * W; l += 32) {             // 3W > 32 for W >= 11
             const int axis = l / W, i = l - axis * W;
             const float nu = axis == 0 ? r.nux : (axis == 1 ? r.nuy : r.nuz);
-            const float *c = scoef + ((axis == 2 ? W : 0) + i) * (deg + 1);
-            float acc = c[deg];
-            for (int m = deg - 1; m >= 0; --m) acc = fmaf(acc, nu, c[m]);
+            const float4 *c = reinterpret_cast<const float4 *>(scoef + ((axis == 2 ? W : 0) + i) * kCoefStride);
+            float acc = c[4].x;                              // Horner from nu^16 down
+#pragma unroll
+            for (int b = 3; b >= 0; --b) {
+                const float4 c4 = c[b];
+                acc = fmaf(acc, nu, c4.w);
+                acc = fmaf(acc, nu, c4.z);
+                acc = fmaf(acc, nu, c4.y);
+                acc = fmaf(acc, nu, c4.x);
+            }
             wt[l] = acc;
         }
         __syncwarp();
         const int64_t t_rel = (int64_t)r.t0 - plane0;       // stack plane of tap c is t_rel + c
+        const bool all_planes = c_lo == 0 && c_hi == W - 1; // uniform: the whole footprint is in the chunk
         float2 f[kPasses][W];
 #pragma unroll
         for (int ps = 0; ps < kPasses; ++ps) {
             const int pair = lane + 32 * ps;
             const int a = pair % W, b = pair / W;
             const bool live = pair < W * W;
-            const float2 *cell = stack + tiled_index(wrap_add(r.s0, live ? b : 0, Np), wrap_add(r.r0, a, Np), Np);
+            const float2 *cell = stack + tiled_index(wrap_add(r.s0, live ? b : 0, Np), wrap_add(r.r0, a, Np), Np) +
+                                 (size_t)t_rel * plane;
+            if (all_planes) {
 #pragma unroll
-            for (int c = 0; c < W; ++c) {
-                f[ps][c] = make_float2(0.f, 0.f);
-                if (live && c >= c_lo && c <= c_hi) f[ps][c] = __ldg(cell + (size_t)(t_rel + c) * plane);
+                for (int c = 0; c < W; ++c) f[ps][c] = live ? __ldg(cell + (size_t)c * plane) : make_float2(0.f, 0.f);
+            } else {
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    f[ps][c] = make_float2(0.f, 0.f);
+                    if (live && c >= c_lo && c <= c_hi) f[ps][c] = __ldg(cell + (size_t)c * plane);
+                }
             }
         }
         float ar = 0.f, ai = 0.f;
