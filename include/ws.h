@@ -227,7 +227,7 @@ ws_status ws_plan_tune(ws_plan_t plan, const double *uvw, const void *vis, const
  * host application owns every allocation, code that must not trigger the
  * synchronisation an allocation can imply).  It computes the same result as
  * ws_degrid, with the same arguments and status codes, but takes all of its
- * per-call scratch (visibility records, tile lists, the corrected image, the
+ * per-call scratch (visibility records, bin lists, the corrected image, the
  * w-plane chunk) from one 64 MiB array in device memory that the library
  * holds on every device that loads it, until the process exits.  It calls no
  * cudaMalloc or cudaFree and allocates nothing else on the device.

@@ -6,7 +6,7 @@
 // device allocations) or code that must not trigger the implicit device
 // synchronisation an allocation can cause.  For them this file runs the same
 // degridding kernels as ws_degrid, but takes every per-call scratch buffer
-// (visibility records, tile lists, counts and occupancy, the corrected
+// (visibility records, bin lists, counts and occupancy, the corrected
 // image, the w-plane chunk and the drop counters) from one fixed, file-scope device
 // array instead of the plan's workspace.  The plan itself (tables made by
 // ws_plan) and the caller's inputs and outputs are used as they are.

@@ -233,10 +233,10 @@ bool fft_make_plan(int n, FftPlan *F) {
 
 // Occupied algorithmic bytes of one call per stage, from the occupancy counts
 // the call copied to h_occ_counts.  Per plane, a column pass reads or writes
-// the occupied tiles (TV x TU cells each) and the N crop rows of every
+// the occupied tiles (tv x TU cells each) and the N crop rows of every
 // occupied (t-tile, u-strip) strip; a row pass the N rows of the occupied
 // strips; gridding writes whole occupied tiles (TT planes) and reads one
-// record and one list entry per (visibility, tile) pair; degridding gathers
+// record and one list entry per (visibility, bin) pair; degridding gathers
 // from the occupied tiles and reads and writes its output once per chunk.
 void add_occupied_bytes(ws_plan_s *p, bool grid, int64_t M) {
     const Launch &L = p->L;
@@ -393,7 +393,7 @@ ws_status ensure_capacity(ws_plan_s *p, int64_t M, bool grid) {
         p->bytes -= p->list_cap * 4;
         p->list_cap = 0;
         cudaError_t e = dev_alloc(&p->d_list, (size_t)need, &p->bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "allocating tile lists");
+        if (e != cudaSuccess) return cuda_fail(e, "allocating bin lists");
         p->list_cap = need;
     }
     return WS_OK;

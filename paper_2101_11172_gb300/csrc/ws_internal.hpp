@@ -145,7 +145,7 @@ struct ws_plan_s {
     unsigned long long *h_drop = nullptr;   // pinned mirror
     int wait_polls = ws::kWaitPolls;        // limit of inv_rows' first wait per plane (WS_WAIT_POLLS)
     // visibility set bound by ws_plan_bind_uvw: records (degridding form) and
-    // both directions' tile lists, made once for that uvw
+    // both directions' bin lists, made once for that uvw
     const double *b_uvw = nullptr;
     int64_t b_M = -1;
     ws::VisRec *d_brec = nullptr;
