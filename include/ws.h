@@ -77,19 +77,19 @@ enum {
                                       gridding sums with FP64 atomics, so it is reproducible to FP64
                                       rounding, not bit for bit); N' must be a power of two <= 4096.  Not for ws_plan_original, batches,
                                       ws_plan_bind_uvw, ws_plan_tune or ws_degrid_noalloc. */
-    WS_FLAG_DETERMINISTIC = 1u << 6 /* bit-for-bit reproducible gridding: each gridding tile sums in 64-bit
-                                      fixed point (a per-tile power-of-two scale keeps every sum below
-                                      2^62, resolution about 1e-19 of the tile's largest possible sum), so
-                                      ws_grid's dirty image does not depend on the order of the
-                                      visibilities or of the GPU's atomics.  Slower gridding (twice the
-                                      shared memory per tile); degridding is deterministic anyway.  For
+    WS_FLAG_DETERMINISTIC = 1u << 6 /* bit-for-bit reproducible gridding: each gridding CTA sums its tile
+                                      column in 64-bit fixed point (a power-of-two scale per column keeps
+                                      every sum below 2^62, resolution about 1e-19 of the column's largest
+                                      possible sum), so ws_grid's dirty image does not depend on the order
+                                      of the visibilities or of the GPU's atomics.  Slower gridding (twice
+                                      the shared memory per CTA); degridding is deterministic anyway.  For
                                       the FP32 path (not WS_FLAG_FP64 plans). */
 };
 
 /* Stages of one call, in execution order (Algorithm 5 / Algorithm 6 steps). */
 enum {
     WS_STAGE_PREP = 0,      /* scale u, v, w; first taps; offsets nu; pre-phase */
-    WS_STAGE_BIN,           /* counting sort of visibilities into gridding tiles */
+    WS_STAGE_BIN,           /* counting sort of visibilities into bins; stack occupancy */
     WS_STAGE_GRID3D,        /* Alg. 5 steps 2-3a: 3-D least-misfit gridding into the w-stack */
     WS_STAGE_COLS_INV,      /* Alg. 5 steps 3b-3c, first half: inverse DFT along v, crop rows */
     WS_STAGE_ROWS_INV,      /* Alg. 5 steps 3b-5, second half: inverse DFT along u, crop,
@@ -185,7 +185,7 @@ ws_status ws_grid(ws_plan_t plan, const double *uvw, const void *vis, int64_t M,
 
 /* Bind a visibility coordinate set to the plan.  The tap rule of Section 3.3,
  * the offsets nu, the pre-phase exp(2 pi i w (n0 - 1)) and the sort of the
- * visibilities into gridding tiles depend on uvw alone, so a consumer that
+ * visibilities into bins depend on uvw alone, so a consumer that
  * calls ws_grid and ws_degrid many times on the same uvw (conjugate
  * gradients, autograd, any iterative imager) can have them made once.  This
  * call makes them for both directions, with the occupancy of the w-stack,
