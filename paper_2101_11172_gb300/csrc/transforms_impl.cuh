@@ -421,9 +421,11 @@ inline size_t smem_fwd_rows(const FftPlan &F, int N, bool step) {
 // fwd_rows steps its screen where the two extra rows still leave room for two
 // CTAs per SM
 inline bool fwd_rows_step(const FftPlan &F, int N) { return smem_fwd_rows(F, N, true) <= kTwoCtaSmem; }
-// CTAs per image row in fwd_rows: enough rows x groups for about eight CTAs per SM
+// CTAs per image row in fwd_rows (each takes an equal share of the planes):
+// enough rows x groups for about 32 CTAs per SM over the launch, so the SMs
+// that finish first in the last round idle for a short CTA, not a long one
 inline int row_groups(int N, int planes, int sms) {
-    const int want = (8 * sms + N - 1) / N;
+    const int want = (32 * sms + N - 1) / N;
     return want < 1 ? 1 : (want > planes ? (planes > 0 ? planes : 1) : want);
 }
 inline size_t smem_rows(const FftPlan &F, int N) {
