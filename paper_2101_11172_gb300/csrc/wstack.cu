@@ -677,7 +677,7 @@ constexpr int kDegridThreads = 256;
 // flight.  The polynomial table sits in shared memory for the weights.  Each
 // chunk adds its planes' share to vis, in chunk order.
 template <int W>
-__global__ void __launch_bounds__(kDegridThreads, W <= 6 ? 5 : (W <= 8 ? 4 : 1))
+__global__ void __launch_bounds__(kDegridThreads, W <= 6 ? 5 : (W <= 8 ? 3 : 1))
 degrid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *__restrict__ rec,
                 const uint32_t *__restrict__ order, const uint32_t *__restrict__ n_order,
                 const float2 *__restrict__ stack, int plane0, int planes, float2 *__restrict__ vis) {
