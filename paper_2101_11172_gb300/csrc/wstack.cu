@@ -396,10 +396,14 @@ __device__ __forceinline__ void add_row(unsigned re, unsigned im, const float (&
 // most entries, start first and do not trail the launch.
 __device__ __forceinline__ int centre_first(int j, int n) { return (j & 1) ? n - 1 - (j >> 1) : (j >> 1); }
 
-// Writes out the ring's slices (t-tiles) s in [from, to) and clears their
-// planes, when the ring holds planes [from TT, from TT + RP): a slice that the
-// chunk owns and a footprint touched (tile_occ) goes to the stack, its planes
-// past the ring's end as zeros (no footprint reached them).
+// Writes out the ring's slices (t-tiles) s in [from, to), when the ring holds
+// planes [from TT, from TT + RP): a slice that the chunk owns and a footprint
+// touched (tile_occ) goes to the stack, its planes past the ring's end as
+// zeros (no footprint reached them).  With `clear`, each thread zeroes the
+// ring cells it has just read, which leaves the slices' ring planes zero for
+// the planes that take their slots: every other cell of those planes is zero
+// already (a slice no footprint touched, or outside the chunk, received no
+// contribution, and padding cells never do).
 template <int W, int R, bool DET>
 __device__ __forceinline__ void flush_slices(int from, int to, const Launch &L, int tv, int tu, int chunk_tt0,
                                              int chunk_ntt, const uint8_t *__restrict__ tile_occ, int scale,
@@ -421,32 +425,22 @@ __device__ __forceinline__ void flush_slices(int from, int to, const Launch &L, 
             if (t < ring_end) {
                 const int cell = (t % RP) * PS + lr * kRowPad + lc;
                 if constexpr (DET) {
-                    const long long *qre = reinterpret_cast<const long long *>(smem + Sm::re);
-                    const long long *qim = reinterpret_cast<const long long *>(smem + Sm::im);
+                    long long *qre = reinterpret_cast<long long *>(smem + Sm::re);
+                    long long *qim = reinterpret_cast<long long *>(smem + Sm::im);
                     v = make_float4(ldexpf(__ll2float_rn(qre[cell]), -scale), ldexpf(__ll2float_rn(qim[cell]), -scale),
                                     ldexpf(__ll2float_rn(qre[cell + 1]), -scale),
                                     ldexpf(__ll2float_rn(qim[cell + 1]), -scale));
+                    if (clear) qre[cell] = qim[cell] = qre[cell + 1] = qim[cell + 1] = 0;
                 } else {
-                    const float *sre = reinterpret_cast<const float *>(smem + Sm::re);
-                    const float *sim = reinterpret_cast<const float *>(smem + Sm::im);
+                    float *sre = reinterpret_cast<float *>(smem + Sm::re);
+                    float *sim = reinterpret_cast<float *>(smem + Sm::im);
                     v = make_float4(sre[cell], sim[cell], sre[cell + 1], sim[cell + 1]);
+                    if (clear) sre[cell] = sim[cell] = sre[cell + 1] = sim[cell + 1] = 0.f;
                 }
             }
             float2 *dst = stack + (size_t)(t - chunk_tt0 * TT) * plane + tiled_index(tv * R + lr, tu * TU + lc, L.Np);
             *reinterpret_cast<float4 *>(dst) = v;
         }
-    }
-    if (!clear) return;
-    __syncthreads();                                  // every cell is read before any is cleared
-    // planes [from TT, min(to TT, ring_end)), consecutive ring slots mod RP
-    constexpr int V4 = PS * Sm::ES / 16;              // 16-byte words per ring plane and component
-    const int t0 = from * TT, np = min(to * TT, ring_end) - t0;
-    float4 *qre = reinterpret_cast<float4 *>(smem + Sm::re), *qim = reinterpret_cast<float4 *>(smem + Sm::im);
-    for (int i = threadIdx.x; i < np * V4; i += kGridThreads) {
-        const int j = i / V4, w = i - j * V4;
-        const int slot = (t0 + j) % RP;
-        qre[slot * V4 + w] = make_float4(0.f, 0.f, 0.f, 0.f);
-        qim[slot * V4 + w] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
