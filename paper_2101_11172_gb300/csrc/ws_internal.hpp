@@ -43,7 +43,7 @@ constexpr int kMaxDeg = 16;
 // its v and w weights).
 constexpr int kGridThreads = 256;
 constexpr int kGridWarps = kGridThreads / 32;
-constexpr int kChunk = 16;
+constexpr int kChunk = 4;
 constexpr int kRowPad = TU + 1;
 constexpr int kCoefStride = 20;
 constexpr size_t kMaxGridSmem = 227 * 1024;     // dynamic shared memory of one CTA
@@ -66,11 +66,14 @@ WS_HD constexpr size_t grid_smem_bytes(int W, int rows, bool det) {
            + (size_t)kGridWarps * kChunk * stage_stride(W) * 4                    // staged weights
            + (size_t)kGridWarps * kChunk * (16 + 8 + 16);                         // items, values, nu
 }
-// CTAs of the gridding kernel that fit on one SM (1 KB reserved per CTA), at most 4
+// CTAs of the gridding kernel that fit on one SM (1 KB reserved per CTA), at
+// most 6.  Gridding is latency-bound and gains from every CTA that fits: on the
+// survey (W = 7, 16-row tiles) 13.2 ms at 3 CTAs per SM, 11.0 at 4, 10.2 at 5 and
+// 10.1 at 6, where the 4-entry chunks and 40 registers just fit.
 WS_HD constexpr int grid_ctas_per_sm(int W, int rows, bool det) {
     return (int)(kSmemPerSM / (grid_smem_bytes(W, rows, det) + 1024)) < 1 ? 1
-           : (int)(kSmemPerSM / (grid_smem_bytes(W, rows, det) + 1024)) > 4
-               ? 4
+           : (int)(kSmemPerSM / (grid_smem_bytes(W, rows, det) + 1024)) > 6
+               ? 6
                : (int)(kSmemPerSM / (grid_smem_bytes(W, rows, det) + 1024));
 }
 // Per-call device counters: visibilities dropped for non-finite u, v; for w
