@@ -304,8 +304,6 @@ __global__ void scan_add_kernel(uint32_t *__restrict__ out, const uint32_t *__re
 // ---------------------------------------------------------------------------
 static_assert(kMaxDeg + 1 <= kCoefStride && kCoefStride % 4 == 0 && kMaxDeg == 16,
               "the Horner steps below read coefficients 0..16 as five float4");
-static_assert(plane_stride(16) % 4 == 0 && plane_stride(32) % 4 == 0 && plane_stride(64) % 4 == 0,
-              "ring planes are cleared in 16-byte stores");
 static_assert(kMaxW <= 15, "tap counts and first taps are packed in 4 bits");
 static_assert(ring_planes(kMaxW) <= 31, "ring slots are packed in 5 bits");
 constexpr int kGeneral = -1;                       // item shape: the part wraps an axis of a small grid
@@ -472,7 +470,7 @@ grid3d_kernel(Launch L, const float *__restrict__ coef, int deg, const VisRec *_
     float *scoef = reinterpret_cast<float *>(smem + Sm::coef);
     {
         float4 *qre = reinterpret_cast<float4 *>(smem + Sm::re), *qim = reinterpret_cast<float4 *>(smem + Sm::im);
-        for (int i = threadIdx.x; i < RP * PS * ES / 16; i += kGridThreads) {
+        for (int i = threadIdx.x; i < (int)(ring_bytes(W, R, DET) / 16); i += kGridThreads) {
             qre[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             qim[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
