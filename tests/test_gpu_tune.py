@@ -109,3 +109,32 @@ def test_tiles_spanning_the_whole_grid(dev, tmp_path, monkeypatch):
     assert rel(v, v_ref) < tol and rel(d, d_ref) < tol, (rel(v, v_ref), rel(d, d_ref))
     assert_elementwise(v, v_ref, tol, "degrid, N' = 32, 32-row tiles")
     assert_elementwise(d, d_ref, tol, "grid, N' = 32, 32-row tiles")
+
+
+def test_deterministic_plans_skip_tiles_whose_ring_does_not_fit(dev, tmp_path, monkeypatch):
+    # deterministic gridding sums in 64-bit cells: at W = 7 a 64-row tile's ring
+    # of planes would need about 250 KB of shared memory, so the tuner leaves that
+    # shape out and a cache entry asking for it is ignored
+    from paper_2101_11172_gb300 import WS_FLAG_DETERMINISTIC
+    from paper_2101_11172_gb300.wstack import Plan
+    c = case(N=128, M=4000, wfac=24.0, seed=31)
+    uvw, vis, img = _tensors(c, dev)
+    cache = tmp_path / "tune.json"
+    with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], flags=WS_FLAG_DETERMINISTIC,
+              device=dev) as p:
+        rows = p.tune(uvw, vis, img, cache_path=str(cache))
+        assert rows in (16, 32)
+    data = json.loads(cache.read_text())
+    (key, entry), = data.items()
+    assert set(entry["ms"]) == {"16", "32"}
+    data[key]["tile_rows"] = 64
+    cache.write_text(json.dumps(data))
+    monkeypatch.setenv("WS_TUNE_CACHE", str(cache))
+    with Plan(c["N"], c["x0"], c["W"], c["fov"], c["w_min"], c["w_max"], flags=WS_FLAG_DETERMINISTIC,
+              device=dev) as p:
+        assert p.tile_rows == 16
+        d = p.grid(uvw, vis).cpu().numpy().astype(np.complex128)
+    g, lm, _, d_ref = oracle_pair(c)
+    tol = tol_for(c["W"], g.x0)
+    assert rel(d, d_ref) < tol
+    assert_elementwise(d, d_ref, tol, "deterministic grid after an ignored 64-row cache entry")
