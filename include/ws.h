@@ -214,7 +214,9 @@ ws_status ws_plan_bind_uvw(ws_plan_t plan, const double *uvw, int64_t M, ws_stre
  * to, that JSON file under the key "<GPU name>|N'=<N'>|W=<W>" (a cached
  * entry skips the timing).  ws_plan and ws_batch_create apply the cached
  * entry for their (N', W) when the environment variable WS_TUNE_CACHE names
- * the file.  Re-tiling drops a bound visibility set.  The tuning allocates
+ * the file; an entry the plan cannot take (rows that do not divide N', or a
+ * gridding ring too large for shared memory, as 64 rows are for deterministic
+ * plans at W = 7) is ignored, and the tuner does not time such shapes.  Re-tiling drops a bound visibility set.  The tuning allocates
  * scratch outputs and synchronises the device; call it at set-up, not in a
  * loop.  The paper has no counterpart: tile shapes are a property of this
  * GPU implementation. */
