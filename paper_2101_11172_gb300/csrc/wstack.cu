@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "ws_internal.hpp"
@@ -882,15 +883,17 @@ cudaError_t launch_degrid_chunk(const ws_plan_s *p, int chunk, int planes, int64
     if (M == 0) return cudaSuccess;
     // resident CTAs only (the kernel loops over the visibilities), at most one warp per visibility
     const int64_t want = blocks_for(M * 32, kDegridThreads);
+    // CTAs per SM by (device, W), looked up once: the plan's device is current here
     auto resident = [&](auto kernel, int w) {
-        static int per_sm[kMaxW + 1] = {};
-        if (per_sm[w] == 0) {
-            int b = 0;
+        constexpr int kDevices = 64;
+        static std::atomic<int> per_sm[kDevices][kMaxW + 1];
+        int b = p->dev >= 0 && p->dev < kDevices ? per_sm[p->dev][w].load(std::memory_order_relaxed) : 0;
+        if (b == 0) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kDegridThreads, 0) != cudaSuccess || b < 1)
                 b = 1;
-            per_sm[w] = b;
+            if (p->dev >= 0 && p->dev < kDevices) per_sm[p->dev][w].store(b, std::memory_order_relaxed);
         }
-        return (unsigned)std::min<int64_t>(want, (int64_t)p->sms * per_sm[w]);
+        return (unsigned)std::min<int64_t>(want, (int64_t)p->sms * b);
     };
 #define WS_DEGRID_CASE(w)                                                                                     \
     case w:                                                                                                  \
