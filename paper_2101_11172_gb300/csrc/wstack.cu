@@ -41,59 +41,63 @@ __device__ __forceinline__ int wrap_index(double x, int n) {
 __global__ void prep_kernel(Launch L, const double *__restrict__ uvw, const float2 *__restrict__ vis,
                             int64_t M, int grid, VisRec *__restrict__ rec,
                             unsigned long long *__restrict__ drop) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= M) return;
-    double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
-    // Section 5.4, real sky: V(u, v, w) = conj V(-u, -v, -w), so w < 0 is gridded at
-    // -(u, v, w) with the conjugate value (and degridded there, conjugated afterwards)
-    const bool folded = L.fold && w < 0.0;
-    if (folded) {
-        u = -u;
-        v = -v;
-        w = -w;
-    }
+    // a grid-stride loop: the plan's constants in FP64 (W / 2, offsets) are formed
+    // once per thread, not once per visibility (FP64 arithmetic is slow here)
     const int W = L.W;
-    VisRec r;
-    r.r0 = r.s0 = 0;
-    r.t0 = -1;
-    r.nux = r.nuy = r.nuz = 0.f;
-    r.vre = r.vim = 0.f;
-    const double up = u * L.uv_scale, vp = v * L.uv_scale, wp = w * L.nscale;
-    if (!(fabs(up) < 1e15) || !(fabs(vp) < 1e15)) {   // also catches NaN
-        atomicAdd(&drop[0], 1ull);
+    const double half_w = 0.5 * W, half_wm1 = 0.5 * (W - 1), t_off = (double)(W - 1) + L.t_lo;
+    const double t_max = (double)(L.Nw - W);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < M; k += (int64_t)gridDim.x * blockDim.x) {
+        double u = uvw[3 * k], v = uvw[3 * k + 1], w = uvw[3 * k + 2];
+        // Section 5.4, real sky: V(u, v, w) = conj V(-u, -v, -w), so w < 0 is gridded at
+        // -(u, v, w) with the conjugate value (and degridded there, conjugated afterwards)
+        const bool folded = L.fold && w < 0.0;
+        if (folded) {
+            u = -u;
+            v = -v;
+            w = -w;
+        }
+        VisRec r;
+        r.r0 = r.s0 = 0;
+        r.t0 = -1;
+        r.nux = r.nuy = r.nuz = 0.f;
+        r.vre = r.vim = 0.f;
+        const double up = u * L.uv_scale, vp = v * L.uv_scale, wp = w * L.nscale;
+        if (!(fabs(up) < 1e15) || !(fabs(vp) < 1e15)) {   // also catches NaN
+            atomicAdd(&drop[0], 1ull);
+            rec[k] = r;
+            continue;
+        }
+        const double ft = floor(wp + half_w);
+        const double t0 = ft - t_off;
+        if (!(t0 >= 0.0 && t0 <= t_max)) {                 // NaN w fails too
+            atomicAdd(&drop[1], 1ull);
+            rec[k] = r;
+            continue;
+        }
+        const double fu = floor(up + half_w), fv = floor(vp + half_w);
+        const double ru = fu - (W - 1), rv = fv - (W - 1);
+        r.r0 = wrap_index(ru, L.Np);
+        r.s0 = wrap_index(rv, L.Np);
+        r.t0 = (int)t0;
+        r.nux = (float)(up + half_wm1 - fu);
+        r.nuy = (float)(vp + half_wm1 - fv);
+        r.nuz = (float)(wp + half_wm1 - ft);
+        // pre-phase exp(+2 pi i w (n0 - 1)), argument reduced in FP64
+        double turns = w * L.n0m1;
+        turns -= rint(turns);
+        float s, c;
+        sincospif(2.0f * (float)turns, &s, &c);
+        if (grid) {
+            float2 V = vis[k];
+            if (folded) V.y = -V.y;
+            r.vre = V.x * c - V.y * s;
+            r.vim = V.x * s + V.y * c;
+        } else {
+            r.vre = c;          // conjugate phase applied after degridding
+            r.vim = -s;
+        }
         rec[k] = r;
-        return;
     }
-    const double ft = floor(wp + 0.5 * W);
-    const double t0 = ft - (W - 1) - L.t_lo;
-    if (!(t0 >= 0.0 && t0 + W <= (double)L.Nw)) {      // NaN w fails too
-        atomicAdd(&drop[1], 1ull);
-        rec[k] = r;
-        return;
-    }
-    const double fu = floor(up + 0.5 * W), fv = floor(vp + 0.5 * W);
-    const double ru = fu - (W - 1), rv = fv - (W - 1);
-    r.r0 = wrap_index(ru, L.Np);
-    r.s0 = wrap_index(rv, L.Np);
-    r.t0 = (int)t0;
-    r.nux = (float)(up + 0.5 * (W - 1) - fu);
-    r.nuy = (float)(vp + 0.5 * (W - 1) - fv);
-    r.nuz = (float)(wp + 0.5 * (W - 1) - ft);
-    // pre-phase exp(+2 pi i w (n0 - 1)), argument reduced in FP64
-    double turns = w * L.n0m1;
-    turns -= rint(turns);
-    float s, c;
-    sincospif(2.0f * (float)turns, &s, &c);
-    if (grid) {
-        float2 V = vis[k];
-        if (folded) V.y = -V.y;
-        r.vre = V.x * c - V.y * s;
-        r.vim = V.x * s + V.y * c;
-    } else {
-        r.vre = c;          // conjugate phase applied after degridding
-        r.vim = -s;
-    }
-    rec[k] = r;
 }
 
 // Gridding records of a bound visibility set: the set's records hold the
@@ -776,7 +780,8 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 cudaError_t launch_prep(const ws_plan_s *p, const double *uvw, const float2 *vis, int64_t M, bool grid,
                         cudaStream_t s) {
     if (M == 0) return cudaSuccess;
-    prep_kernel<<<blocks_for(M, 256), 256, 0, s>>>(p->L, uvw, vis, M, grid ? 1 : 0, p->d_rec, p->d_drop);
+    const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(M, 256), (int64_t)p->sms * 8);
+    prep_kernel<<<blocks, 256, 0, s>>>(p->L, uvw, vis, M, grid ? 1 : 0, p->d_rec, p->d_drop);
     return cudaGetLastError();
 }
 
